@@ -1,0 +1,176 @@
+"""Python binding of the picount C ABI (include/picount.h).
+
+Argument marshalling only: every step of every computation runs in the CUDA
+library ``libpicount.so`` built for sm_103a.  There is no CPU fallback: if
+the library is missing or cannot be loaded, importing ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpicount.so")
+
+PC_OK = 0
+ERRORS = {-1: "PC_EINVAL", -2: "PC_ERANGE", -3: "PC_ENOMEM", -4: "PC_ECUDA", -5: "PC_ETIMEOUT", -6: "PC_EOVERFLOW"}
+
+# every symbol declared in include/picount.h
+SYMBOLS = ["pc_create", "pc_destroy", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
+           "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats", "pc_strerror", "pc_last_error", "pc_version"]
+
+
+class PcI128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int64), ("hi", ctypes.c_int64)]
+
+    def value(self) -> int:
+        return (self.hi << 64) + (self.lo & ((1 << 64) - 1))
+
+
+class PcParams(ctypes.Structure):
+    _fields_ = [("seg_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("threads", ctypes.c_uint32),
+                ("alpha", ctypes.c_uint32), ("c", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+
+
+class PcStats(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_uint64), ("y", ctypes.c_uint64), ("z", ctypes.c_uint64), ("a", ctypes.c_uint64),
+                ("B", ctypes.c_uint64), ("c", ctypes.c_uint32), ("seg_bytes", ctypes.c_uint32),
+                ("segments", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("hard_leaves", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64),
+                ("ms_tables", ctypes.c_double), ("ms_s1", ctypes.c_double), ("ms_trivial", ctypes.c_double),
+                ("ms_easy", ctypes.c_double), ("ms_hard", ctypes.c_double), ("ms_p2", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_hard_sieve", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libpicount.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libpicount.so not built: run paper_1503_01839_gb300/build.py "
+                                   "(or __graft_entry__.build()) first")
+            L = ctypes.CDLL(LIB_PATH)
+            u64, u32, p = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+            L.pc_create.argtypes = [ctypes.POINTER(p), ctypes.c_int, ctypes.POINTER(PcParams)]
+            L.pc_destroy.argtypes = [p]
+            L.pc_destroy.restype = None
+            L.pc_set_stream.argtypes = [p, p]
+            L.pc_pi_count.argtypes = [p, u64, u32, ctypes.POINTER(u64)]
+            L.pc_phi.argtypes = [p, u64, u64, ctypes.POINTER(u64)]
+            L.pc_s2_hard.argtypes = [p, u64, u64, u32, ctypes.POINTER(PcI128)]
+            L.pc_p2.argtypes = [p, u64, u64, ctypes.POINTER(u64)]
+            L.pc_leaf_sums.argtypes = [p, u64, u64, u32, u64, ctypes.POINTER(PcI128)]
+            L.pc_pi_count_batch.argtypes = [p, p, ctypes.c_size_t, p, p]
+            L.pc_last_stats.argtypes = [p, ctypes.POINTER(PcStats)]
+            L.pc_strerror.argtypes = [ctypes.c_int]
+            L.pc_strerror.restype = ctypes.c_char_p
+            L.pc_last_error.argtypes = [p]
+            L.pc_last_error.restype = ctypes.c_char_p
+            L.pc_version.restype = ctypes.c_char_p
+            for name in ("pc_create", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
+                         "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+class PicountError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Context:
+    """One library context (device tables + scratch) on one CUDA device."""
+
+    def __init__(self, device: int = 0, seg_bytes: int = 0, ctas_per_sm: int = 0, threads: int = 0,
+                 alpha: int = 0, c: int = 0):
+        self._L = lib()
+        prm = PcParams(seg_bytes, ctas_per_sm, threads, alpha, c)
+        h = ctypes.c_void_p()
+        rc = self._L.pc_create(ctypes.byref(h), device, ctypes.byref(prm))
+        if rc != PC_OK:
+            raise PicountError(rc, "pc_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.pc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc: int):
+        if rc != PC_OK:
+            raise PicountError(rc, self._L.pc_last_error(self._h).decode())
+
+    def set_stream(self, stream_handle: int | None):
+        self._check(self._L.pc_set_stream(self._h, ctypes.c_void_p(stream_handle or 0)))
+
+    def pi_count(self, x: int, alpha: int = 0) -> int:
+        out = ctypes.c_uint64()
+        self._check(self._L.pc_pi_count(self._h, x, alpha, ctypes.byref(out)))
+        return out.value
+
+    def phi(self, x: int, a: int) -> int:
+        out = ctypes.c_uint64()
+        self._check(self._L.pc_phi(self._h, x, a, ctypes.byref(out)))
+        return out.value
+
+    def s2_hard(self, x: int, y: int, c: int) -> int:
+        out = PcI128()
+        self._check(self._L.pc_s2_hard(self._h, x, y, c, ctypes.byref(out)))
+        return out.value()
+
+    def p2(self, x: int, y: int) -> int:
+        out = ctypes.c_uint64()
+        self._check(self._L.pc_p2(self._h, x, y, ctypes.byref(out)))
+        return out.value
+
+    def leaf_sums(self, x: int, y: int, c: int, a: int = 0) -> dict:
+        out = (PcI128 * 5)()
+        self._check(self._L.pc_leaf_sums(self._h, x, y, c, a, out))
+        v = [o.value() for o in out]
+        return {"S1": v[0], "S2_triv": v[1], "S2_easy": v[2], "S2_hard": v[3], "P2": v[4]}
+
+    def pi_count_batch(self, xs, out=None, stream_handle: int | None = None):
+        """xs: sequence of ints (host), or a device pointer (int) with n given
+        by len(out) when stream_handle is set."""
+        if stream_handle is None:
+            n = len(xs)
+            arr = (ctypes.c_uint64 * n)(*xs)
+            res = (ctypes.c_uint64 * n)()
+            self._check(self._L.pc_pi_count_batch(self._h, arr, n, res, None))
+            return list(res)
+        xs_ptr, out_ptr, n = xs
+        self._check(self._L.pc_pi_count_batch(self._h, ctypes.c_void_p(xs_ptr), n, ctypes.c_void_p(out_ptr),
+                                              ctypes.c_void_p(stream_handle)))
+        return None
+
+    def stats(self) -> dict:
+        s = PcStats()
+        self._check(self._L.pc_last_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+
+def version() -> str:
+    return lib().pc_version().decode()

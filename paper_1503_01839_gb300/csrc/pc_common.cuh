@@ -1,0 +1,170 @@
+// pc_common.cuh -- shared device/host helpers for the picount CUDA library.
+//
+// Number layout used by every sieve in this library ("mod-30 wheel"): byte i
+// of a bitset stands for the numbers 30*i .. 30*i+29, and bit j of that byte
+// for 30*i + R8[j], R8 = {1,7,11,13,17,19,23,29} (the residues coprime to
+// 2*3*5).  Multiples of 2, 3, 5 are never stored.  This is the wheel of
+// Section 2.1 / 2.2 with c = 3; deeper wheels (7, 11) are applied as
+// periodic byte patterns.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+typedef unsigned long long u64;
+typedef long long i64;
+typedef unsigned int u32;
+typedef int i32;
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+#define PC_HD __host__ __device__ __forceinline__
+
+// ------------------------------------------------------------- wheel tables
+static __constant__ unsigned char c_R8[8] = {1, 7, 11, 13, 17, 19, 23, 29};
+// index of residue r in R8, 255 if r shares a factor with 30
+static __constant__ unsigned char c_IDX30[30] = {
+    255, 0, 255, 255, 255, 255, 255, 1, 255, 255, 255, 2, 255, 3, 255,
+    255, 255, 4, 255, 5, 255, 255, 255, 6, 255, 255, 255, 255, 255, 7};
+// number of R8 residues <= r
+static __constant__ unsigned char c_CNTLE30[30] = {
+    0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 4, 4,
+    4, 4, 5, 5, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7, 8};
+// distance from residue r to the next residue coprime to 30 (strictly greater)
+static __constant__ unsigned char c_NEXT30[30] = {
+    1, 6, 5, 4, 3, 2, 1, 4, 3, 2, 1, 2, 1, 4, 3,
+    2, 1, 2, 1, 4, 3, 2, 1, 6, 5, 4, 3, 2, 1, 2};
+
+// ------------------------------------------------------ exact integer roots
+PC_HD int pc_bitlen(u64 n) { int k = 0; while (n) { k++; n >>= 1; } return k; }
+
+// floor(sqrt(n)) by integer Newton iteration from an upper bound (no FP).
+PC_HD u64 pc_isqrt(u64 n)
+{
+    if (n < 2) return n;
+    u64 x = 1ull << ((pc_bitlen(n) + 1) / 2);
+    for (;;) {
+        u64 y = (x + n / x) >> 1;
+        if (y >= x) break;
+        x = y;
+    }
+    return x;
+}
+
+// floor(cbrt(n)) by integer Newton iteration plus an exact correction.
+PC_HD u64 pc_iroot3(u64 n)
+{
+    if (n < 8) return n ? 1 : 0;
+    u64 x = 1ull << ((pc_bitlen(n) + 2) / 3);
+    for (;;) {
+        u64 y = (2 * x + n / (x * x)) / 3;
+        if (y >= x) break;
+        x = y;
+    }
+    while ((u128)x * x * x > n) x--;
+    while ((u128)(x + 1) * (x + 1) * (x + 1) <= n) x++;
+    return x;
+}
+
+PC_HD u64 pc_min(u64 a, u64 b) { return a < b ? a : b; }
+PC_HD u64 pc_max(u64 a, u64 b) { return a > b ? a : b; }
+
+// ----------------------------------------------------------- lookup tables
+// pi table: mod-30 bitset of the primes in [0, limit] (1 is cleared), one
+// u64 word per 240 numbers, plus pcnt[w] = number of set bits in words < w.
+struct PiTable {
+    const u64* words;
+    const u32* pcnt;
+    u64 limit;
+};
+
+// pi(v) for 0 <= v <= limit.
+__device__ __forceinline__ u64 pi_lookup(const PiTable& t, u64 v)
+{
+    u64 small = (v >= 2) + (v >= 3) + (v >= 5);
+    u64 w = v / 240;
+    u32 r = (u32)(v - w * 240);
+    u32 e = 8 * (r / 30) + c_CNTLE30[r % 30];
+    u64 mask = e >= 64 ? ~0ull : ((1ull << e) - 1);
+    return small + t.pcnt[w] + __popcll(__ldg(t.words + w) & mask);
+}
+
+// rank structure over a plain bitset of [0, limit]: rank(v) = #set bits <= v.
+struct RankTable {
+    const u64* bits;
+    const u32* cnt;   // set bits in words < w
+    u64 limit;
+};
+
+__device__ __forceinline__ u64 rank_lookup(const RankTable& t, u64 v)
+{
+    if (v > t.limit) v = t.limit;
+    u64 w = v >> 6;
+    u32 sh = (u32)(v & 63);
+    u64 mask = sh == 63 ? ~0ull : ((1ull << (sh + 1)) - 1);
+    return t.cnt[w] + __popcll(__ldg(t.bits + w) & mask);
+}
+
+// squarefree m-list, ascending m.  info = (lpf_index << 1) | (mu == -1).
+struct MList {
+    const u32* m;
+    const u32* info;
+    const u32* gpf;   // prime index of the greatest prime factor
+    u64 n;
+    u64 limit;        // every squarefree m <= limit with lpf(m) > p_cmin is listed
+    u32 cmin;
+};
+
+// ------------------------------------------------------------- reductions
+__device__ __forceinline__ i64 warp_sum_i64(i64 v)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ i128 warp_sum_i128(i128 v)
+{
+    u64 lo = (u64)v;
+    i64 hi = (i64)(v >> 64);
+    for (int o = 16; o; o >>= 1) {
+        u64 lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        i64 hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        u64 s = lo + lo2;
+        hi = hi + hi2 + (s < lo);
+        lo = s;
+    }
+    return ((i128)hi << 64) | (i128)lo;
+}
+
+// CTA-wide i128 sum; result valid in thread 0.  scratch: >= 32 i128.
+__device__ __forceinline__ i128 block_sum_i128(i128 v, i128* scratch)
+{
+    v = warp_sum_i128(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    i128 r = 0;
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        r = lane < nw ? scratch[lane] : (i128)0;
+        r = warp_sum_i128(r);
+    }
+    return r;
+}
+
+// --------------------------------------------------------------- results
+// Partial sums are written as i128 into per-block slots and summed by
+// reduce_i128_kernel (pc_engine.cu).
+struct I128Pair { i64 lo; i64 hi; };
+
+__device__ __forceinline__ void store_i128(I128Pair* p, i128 v)
+{
+    p->lo = (i64)(u64)v;
+    p->hi = (i64)(v >> 64);
+}
+
+__device__ __forceinline__ i128 load_i128(const I128Pair* p)
+{
+    return ((i128)p->hi << 64) | (i128)(u64)p->lo;
+}

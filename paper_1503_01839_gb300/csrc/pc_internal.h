@@ -1,0 +1,138 @@
+// pc_internal.h -- host-side declarations shared by the library's .cu files.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+#include <cuda_runtime.h>
+
+#include "picount.h"
+#include "pc_common.cuh"
+
+// ------------------------------------------------------------------ errors
+// Every CUDA call goes through PC_CUDA; on failure the enclosing function
+// returns PC_ECUDA after recording the message in the context.
+void pc_set_error(pc_ctx* ctx, const char* fmt, ...);
+
+#define PC_CUDA(ctx, call)                                                     \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            pc_set_error((ctx), "%s failed: %s (%s:%d)", #call,                \
+                         cudaGetErrorString(e_), __FILE__, __LINE__);          \
+            return PC_ECUDA;                                                   \
+        }                                                                      \
+    } while (0)
+
+#define PC_TRY(expr)                                                           \
+    do {                                                                       \
+        int r_ = (expr);                                                       \
+        if (r_ != PC_OK) return r_;                                            \
+    } while (0)
+
+// Launch check: a launch error (bad configuration) is reported at once.
+#define PC_LAUNCHED(ctx) PC_CUDA(ctx, cudaGetLastError())
+
+// --------------------------------------------------------------- buffers
+// Grow-only device buffer owned by the context.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    template <class T> T* as() const { return (T*)p; }
+};
+
+int buf_reserve(pc_ctx* ctx, DevBuf& b, size_t bytes);
+void buf_free(DevBuf& b);
+
+// ----------------------------------------------------------------- tables
+struct Tables {
+    // primes <= 65536 (bootstrap), u32, ascending, 0-based
+    DevBuf small_primes;
+    u32 n_small = 0;
+    // pi table over [0, pi_limit]
+    u64 pi_limit = 0;
+    DevBuf pi_words, pi_pcnt;
+    // primes[1..nprimes] (u32), primes[0] = 1, primes[nprimes+1] = next prime
+    u64 prime_limit = 0;
+    u64 nprimes = 0;
+    DevBuf primes;
+    // squarefree m-list over [2, ml_limit] with lpf > p_cmin
+    u64 ml_limit = 0;
+    u32 ml_cmin = 99;
+    u64 ml_n = 0;
+    DevBuf ml_m, ml_info, ml_gpf, rank_bits, rank_cnt;
+    // phi(., c) residue tables for the primorial of c (c = 0..7)
+    DevBuf phiT[8];
+    bool phiT_ok[8] = {false, false, false, false, false, false, false, false};
+
+    PiTable pi() const { return PiTable{pi_words.as<u64>(), pi_pcnt.as<u32>(), pi_limit}; }
+    RankTable rank() const { return RankTable{rank_bits.as<u64>(), rank_cnt.as<u32>(), ml_limit}; }
+    MList mlist() const { return MList{ml_m.as<u32>(), ml_info.as<u32>(), ml_gpf.as<u32>(), ml_n, ml_limit, ml_cmin}; }
+};
+
+// ---------------------------------------------------------------- context
+struct pc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;   // stream every kernel of this context uses
+    cudaStream_t own_stream = nullptr;
+    pc_params params{};
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    Tables T;
+    // scratch (grow-only)
+    DevBuf seg_b, seg_off, counts, tallies, acc_seg, partials, result, misc, scan_tmp, queue;
+    DevBuf easy_rng, easy_chunk_off;
+    // pinned host staging for small results
+    void* host_stage = nullptr;
+    pc_stats stats{};
+    char errmsg[512] = {0};
+    cudaEvent_t ev[16];
+    bool ev_ok = false;
+};
+
+// ------------------------------------------------------------------- util
+// out[i] = sum_{j<i} in[j] for i < n, and out[n] = total (out has n+1 slots).
+int scan_exclusive_u32_to_u32(pc_ctx* ctx, const u32* in, u32* out, u64 n);
+int scan_exclusive_u32_to_u64(pc_ctx* ctx, const u32* in, u64* out, u64 n);
+// *out = sum of n i128 values
+int reduce_i128(pc_ctx* ctx, const I128Pair* in, u64 n, I128Pair* out);
+int copy_to_host(pc_ctx* ctx, void* dst, const void* src, size_t bytes);  // synchronizes
+
+// ----------------------------------------------------------------- tables
+// Make sure tables cover pi lookups up to pi_limit, primes up to
+// prime_limit (plus one sentinel prime), and the m-list up to ml_limit with
+// lpf(m) > p_cmin.
+int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 cmin);
+int tables_phi_c(pc_ctx* ctx, u32 c);   // phi(., c) residue table
+// values of pi(v) for a handful of v (v <= pi_limit), synchronizing
+int tables_pi_values(pc_ctx* ctx, const u64* v, u64* out, int n);
+
+// ----------------------------------------------------------------- leaves
+struct LeafProblem {
+    u64 x, y, z;
+    u32 c;        // ordinary-leaf wheel depth
+    u64 a;        // leaves use primes p_b with c < b <= a
+    bool trunc;   // a < pi(y): filter gpf(m) <= p_a
+    u64 piy;      // pi(y)
+    u64 B;        // pi(isqrt z)
+};
+
+// Each adds its sum to *out (device I128Pair) -- out must be zeroed first.
+int run_s1(pc_ctx* ctx, const LeafProblem& P, I128Pair* out);
+int run_trivial(pc_ctx* ctx, const LeafProblem& P, I128Pair* out);
+int run_easy(pc_ctx* ctx, const LeafProblem& P, I128Pair* out);
+int run_hard_smallb(pc_ctx* ctx, const LeafProblem& P, I128Pair* out);
+int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out);
+int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out);
+
+// segment geometry shared by the sieve kernels
+struct SegGeom {
+    u32 seg_bytes;   // bytes per segment (multiple of 128)
+    u64 span;        // numbers per segment = 30 * seg_bytes
+    u64 nseg;
+    int threads;
+    int ctas;
+    size_t smem;
+};
+
+u32 pc_seg_bytes(pc_ctx* ctx);

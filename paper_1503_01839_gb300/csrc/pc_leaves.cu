@@ -1,0 +1,308 @@
+// pc_leaves.cu -- the leaf sums that need no sieve.
+//
+// phi(x, a) = S1 + S2 with (combinatorial method of Section 2, tree
+// truncated at p_a):
+//   S1 = sum over squarefree n <= y, n = 1 or lpf(n) > p_c, gpf(n) <= p_a of
+//        mu(n) * phi(x/n, c)                                 (ordinary leaves)
+//   S2 = sum over c < b <= a, squarefree m with lpf(m) > p_b, gpf(m) <= p_a,
+//        y/p_b < m <= y, of -mu(m) * phi(x/(p_b m), b-1)     (special leaves)
+// For a special leaf let u = x/(p_b m).  u < p_b: phi(u, b-1) = 1 (trivial).
+// p_b <= u < min(p_b^2, y): phi(u, b-1) = pi(u) - b + 2 (easy; the Legendre
+// case of Section 4, with pi(u) from the pi table).  Everything else is a
+// hard leaf, resolved by the main sieve (pc_hard.cu); those with b <= 3 have
+// the closed forms phi(u,0) = u, phi(u,1) = u - u/2, phi(u,2) = u - u/2 - u/3 + u/6.
+// The easy leaves are embarrassingly parallel (Section 3).
+#include "pc_internal.h"
+
+struct LeafArgs {
+    u64 x, y;
+    u32 c;
+    u64 a;
+    bool trunc;
+    PiTable pit;
+    RankTable rk;
+    MList ml;
+    const u32* primes;
+    u64 n_lim;   // list entries with m <= y: [0, n_lim)
+};
+
+static LeafArgs make_args(pc_ctx* ctx, const LeafProblem& P, u64 n_lim)
+{
+    LeafArgs A;
+    A.x = P.x;
+    A.y = P.y;
+    A.c = P.c;
+    A.a = P.a;
+    A.trunc = P.trunc;
+    A.pit = ctx->T.pi();
+    A.rk = ctx->T.rank();
+    A.ml = ctx->T.mlist();
+    A.primes = ctx->T.primes.as<u32>();
+    A.n_lim = n_lim;
+    return A;
+}
+
+// list index range of entries with m <= y
+__global__ void rank_of_kernel(RankTable rk, u64 v, u64* out) { *out = rank_lookup(rk, v); }
+
+static int list_count_upto(pc_ctx* ctx, u64 y, u64* n)
+{
+    PC_TRY(buf_reserve(ctx, ctx->misc, 64 * sizeof(u64)));
+    rank_of_kernel<<<1, 1, 0, ctx->stream>>>(ctx->T.rank(), y, ctx->misc.as<u64>());
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    return copy_to_host(ctx, n, ctx->misc.p, sizeof(u64));
+}
+
+static int grid_for(pc_ctx* ctx) { return ctx->sm_count * 4; }
+
+// ------------------------------------------------------------------- S1
+__global__ void s1_kernel(LeafArgs A, const u32* phiT, u32 Q, I128Pair* part)
+{
+    __shared__ i128 scratch[32];
+    i128 s = 0;
+    auto phic = [&](u64 v) -> u64 {
+        if (A.c == 0) return v;
+        u64 q = v / Q;
+        u32 r = (u32)(v - q * Q);
+        return q * phiT[Q] + phiT[r + 1];
+    };
+    u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) s += (i128)phic(A.x);   // n = 1
+    for (u64 i = tid; i < A.n_lim; i += (u64)gridDim.x * blockDim.x) {
+        u32 info = A.ml.info[i];
+        if ((info >> 1) <= A.c) continue;
+        if (A.trunc && A.ml.gpf[i] > A.a) continue;
+        u64 m = A.ml.m[i];
+        u64 f = phic(A.x / m);
+        if (info & 1) s -= (i128)f; else s += (i128)f;
+    }
+    s = block_sum_i128(s, scratch);
+    if (threadIdx.x == 0) store_i128(part + blockIdx.x, s);
+}
+
+int run_s1(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
+{
+    PC_TRY(tables_phi_c(ctx, P.c));
+    u64 n_lim = 0;
+    PC_TRY(list_count_upto(ctx, P.y, &n_lim));
+    int g = grid_for(ctx);
+    PC_TRY(buf_reserve(ctx, ctx->partials, g * sizeof(I128Pair)));
+    u32 Q = 1;
+    static const u32 P8[8] = {1, 2, 3, 5, 7, 11, 13, 17};
+    for (u32 i = 1; i <= P.c; i++) Q *= P8[i];
+    s1_kernel<<<g, 256, 0, ctx->stream>>>(make_args(ctx, P, n_lim), P.c ? ctx->T.phiT[P.c].as<u32>() : nullptr, Q,
+                                          ctx->partials.as<I128Pair>());
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    return reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out);
+}
+
+// -------------------------------------------------------------- trivial
+// For m the trivial leaves are the b with max(c, pi(T)) < b < lpf_index(m),
+// b <= a, T = max(y/m, isqrt(x/m)): p_b > y/m makes m > y/p_b, and
+// p_b > isqrt(x/m) makes p_b^2 m > x, i.e. u < p_b.
+__global__ void trivial_kernel(LeafArgs A, I128Pair* part)
+{
+    __shared__ i128 scratch[32];
+    i64 s = 0;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < A.n_lim; i += (u64)gridDim.x * blockDim.x) {
+        u32 info = A.ml.info[i];
+        u64 k = info >> 1;
+        if (k <= A.c + 1) continue;
+        if (A.trunc && A.ml.gpf[i] > A.a) continue;
+        u64 m = A.ml.m[i];
+        u64 T = pc_max(A.y / m, pc_isqrt(A.x / m));
+        u64 hi = pc_min(k - 1, A.a);
+        u64 lo = A.c;
+        if (T >= 2) {
+            u64 pt = pi_lookup(A.pit, T);
+            if (pt > lo) lo = pt;
+        }
+        if (hi > lo) {
+            i64 cnt = (i64)(hi - lo);
+            s += (info & 1) ? cnt : -cnt;
+        }
+    }
+    i128 v = block_sum_i128((i128)s, scratch);
+    if (threadIdx.x == 0) store_i128(part + blockIdx.x, v);
+}
+
+int run_trivial(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
+{
+    u64 n_lim = 0;
+    PC_TRY(list_count_upto(ctx, P.y, &n_lim));
+    int g = grid_for(ctx);
+    PC_TRY(buf_reserve(ctx, ctx->partials, g * sizeof(I128Pair)));
+    trivial_kernel<<<g, 256, 0, ctx->stream>>>(make_args(ctx, P, n_lim), ctx->partials.as<I128Pair>());
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    return reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out);
+}
+
+// ----------------------------------------------------------------- easy
+// Leaf ranges per b, then fixed-size chunks of leaves over all b.
+static constexpr u32 EASY_CHUNK = 2048;
+
+struct EasyRange {
+    u64 i0, i1;   // list indices [i0, i1) or prime indices (i0, i1] shifted to [i0+1, i1+1)
+    u32 src;      // 0: m-list, 1: primes
+    u32 pad;
+};
+
+__global__ void easy_ranges_kernel(LeafArgs A, u64 b_lo, u64 nb, EasyRange* rng, u32* nchunk)
+{
+    u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    u64 b = b_lo + t;
+    u64 p = A.primes[b];
+    u64 xp = A.x / p;
+    u64 T = pc_min(p * p, A.y);
+    u64 lo = pc_max(A.y / p, xp / T);
+    u64 hi = pc_min(A.y, xp / p);
+    EasyRange r{0, 0, 0, 0};
+    if (hi > lo) {
+        if (p * p > A.y) {
+            // lpf(m) > p_b and m <= y < p_b^2: m is a prime q, p_b < q <= p_a
+            u64 k0 = pc_max(pi_lookup(A.pit, lo), b);
+            u64 k1 = pc_min(pi_lookup(A.pit, hi), A.a);
+            if (k1 > k0) { r.i0 = k0 + 1; r.i1 = k1 + 1; r.src = 1; }
+        } else {
+            r.i0 = rank_lookup(A.rk, lo);
+            r.i1 = rank_lookup(A.rk, hi);
+            r.src = 0;
+        }
+    }
+    rng[t] = r;
+    nchunk[t] = (u32)((r.i1 - r.i0 + EASY_CHUNK - 1) / EASY_CHUNK);
+}
+
+__global__ void easy_kernel(LeafArgs A, u64 b_lo, u64 nb, const EasyRange* rng, const u64* choff,
+                            u64 nchunks, I128Pair* part)
+{
+    __shared__ i128 scratch[32];
+    __shared__ u64 s_b;
+    i64 s = 0;
+    for (u64 ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        if (threadIdx.x == 0) {
+            // largest t with choff[t] <= ch
+            u64 lo = 0, hi = nb;
+            while (hi - lo > 1) {
+                u64 mid = (lo + hi) >> 1;
+                if (choff[mid] <= ch) lo = mid; else hi = mid;
+            }
+            s_b = lo;
+        }
+        __syncthreads();
+        u64 t = s_b;
+        __syncthreads();
+        u64 b = b_lo + t;
+        EasyRange r = rng[t];
+        u64 start = r.i0 + (ch - choff[t]) * EASY_CHUNK;
+        u64 end = pc_min(r.i1, start + EASY_CHUNK);
+        u64 p = A.primes[b];
+        u64 xp = A.x / p;
+        for (u64 i = start + threadIdx.x; i < end; i += blockDim.x) {
+            u64 m;
+            bool neg;
+            if (r.src) {
+                m = A.primes[i];
+                neg = true;
+            } else {
+                u32 info = A.ml.info[i];
+                if ((info >> 1) <= b) continue;
+                if (A.trunc && A.ml.gpf[i] > A.a) continue;
+                m = A.ml.m[i];
+                neg = info & 1;
+            }
+            u64 u = xp / m;
+            i64 v = (i64)pi_lookup(A.pit, u) - (i64)b + 2;
+            s += neg ? v : -v;
+        }
+    }
+    i128 v = block_sum_i128((i128)s, scratch);
+    if (threadIdx.x == 0) store_i128(part + blockIdx.x, v);
+}
+
+int run_easy(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
+{
+    u64 b_lo = (u64)P.c + 1;
+    if (P.a < b_lo) return PC_OK;
+    u64 nb = P.a - b_lo + 1;
+    PC_TRY(buf_reserve(ctx, ctx->easy_rng, nb * sizeof(EasyRange)));
+    PC_TRY(buf_reserve(ctx, ctx->easy_chunk_off, (nb + 1) * sizeof(u64) + (nb + 1) * sizeof(u32)));
+    u64* choff = ctx->easy_chunk_off.as<u64>();
+    u32* nch = (u32*)(choff + nb + 1);
+    LeafArgs A = make_args(ctx, P, 0);
+    easy_ranges_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>(A, b_lo, nb,
+                                                                              ctx->easy_rng.as<EasyRange>(), nch);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    PC_TRY(scan_exclusive_u32_to_u64(ctx, nch, choff, nb));
+    u64 nchunks = 0;
+    PC_TRY(copy_to_host(ctx, &nchunks, choff + nb, sizeof(u64)));
+    if (nchunks == 0) return PC_OK;
+    int g = ctx->sm_count * 8;
+    PC_TRY(buf_reserve(ctx, ctx->partials, g * sizeof(I128Pair)));
+    easy_kernel<<<g, 256, 0, ctx->stream>>>(A, b_lo, nb, ctx->easy_rng.as<EasyRange>(), choff, nchunks,
+                                            ctx->partials.as<I128Pair>());
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    return reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out);
+}
+
+// ------------------------------------------------------- hard, b <= 3
+__global__ void hard_smallb_kernel(LeafArgs A, u64 b, u64 i0, u64 i1, I128Pair* part)
+{
+    __shared__ i128 scratch[32];
+    i128 s = 0;
+    u64 p = A.primes[b];
+    u64 xp = A.x / p;
+    for (u64 i = i0 + (u64)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += (u64)gridDim.x * blockDim.x) {
+        u32 info = A.ml.info[i];
+        if ((info >> 1) <= b) continue;
+        if (A.trunc && A.ml.gpf[i] > A.a) continue;
+        u64 u = xp / A.ml.m[i];
+        u64 ph;
+        if (b == 1) ph = u;
+        else if (b == 2) ph = u - u / 2;
+        else ph = u - u / 2 - u / 3 + u / 6;
+        if (info & 1) s += (i128)ph; else s -= (i128)ph;
+    }
+    s = block_sum_i128(s, scratch);
+    if (threadIdx.x == 0) store_i128(part + blockIdx.x, load_i128(part + blockIdx.x) + s);
+}
+
+__global__ void smallb_range_kernel(LeafArgs A, u64 b, u64* out)
+{
+    u64 p = A.primes[b];
+    u64 xp = A.x / p;
+    u64 T = pc_min(p * p, A.y);
+    u64 lo = A.y / p;
+    u64 hi = pc_min(A.y, xp / T);
+    out[0] = rank_lookup(A.rk, lo);
+    out[1] = hi > lo ? rank_lookup(A.rk, hi) : out[0];
+}
+
+int run_hard_smallb(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
+{
+    if (P.c >= 3) return PC_OK;
+    int g = grid_for(ctx);
+    PC_TRY(buf_reserve(ctx, ctx->partials, g * sizeof(I128Pair)));
+    PC_CUDA(ctx, cudaMemsetAsync(ctx->partials.p, 0, g * sizeof(I128Pair), ctx->stream));
+    LeafArgs A = make_args(ctx, P, 0);
+    for (u64 b = (u64)P.c + 1; b <= 3 && b <= P.a; b++) {
+        PC_TRY(buf_reserve(ctx, ctx->misc, 64 * sizeof(u64)));
+        smallb_range_kernel<<<1, 1, 0, ctx->stream>>>(A, b, ctx->misc.as<u64>());
+        PC_LAUNCHED(ctx);
+        u64 r[2];
+        PC_TRY(copy_to_host(ctx, r, ctx->misc.p, 2 * sizeof(u64)));
+        if (r[1] > r[0]) {
+            hard_smallb_kernel<<<g, 256, 0, ctx->stream>>>(A, b, r[0], r[1], ctx->partials.as<I128Pair>());
+            PC_LAUNCHED(ctx);
+            ctx->stats.kernel_launches++;
+        }
+        ctx->stats.kernel_launches++;
+    }
+    return reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out);
+}

@@ -1,0 +1,285 @@
+// pc_p2.cu -- P2(x, a) = sum over primes y < p <= isqrt(x) of (pi(x/p) - pi(p) + 1).
+//
+// The values pi(x/p) lie in [isqrt x, z], z = x/y.  The interval [0, z] is
+// sieved in the same mod-30 shared-memory segments as the hard-leaf sieve,
+// by every prime <= isqrt(z), in any order (no leaf needs an intermediate
+// state, so the crossing off is order-free).  In the final state a segment
+// holds phi(., B) locally, B = pi(isqrt z), and for v >= p_B
+//   pi(v) = phi(v, B) + B - 1.
+// Each segment answers the p with x/p inside it by a local count plus a
+// tally of how many p it answered; a scan of the per-segment totals then
+// supplies phi(L_s - 1, B).  The p themselves are read from the pi table.
+#include "pc_internal.h"
+#include "pc_sieve.cuh"
+
+struct P2Args {
+    u64 x, y, z, r;   // r = isqrt(x)
+    u32 B, k0;
+    u64 nseg;
+    u32 seg_bytes;
+    u64 span;
+    PiTable pit;
+    const u32* primes;
+    u32* cnt;         // set bits per segment (final state)
+    u32* tally;       // number of p answered per segment
+    I128Pair* acc;    // sum of local counts per segment
+    u32* queue;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u32* bits = (u32*)smem_raw;
+    const u32 seg_words = A.seg_bytes >> 2;
+    const u32 nblk = A.seg_bytes >> 7;
+    u32* blk = bits + seg_words;
+    u32* pre = blk + nblk;
+    const u64* bits64 = (const u64*)bits;
+    __shared__ u32 patw[80];
+    __shared__ u32 wsum[32];
+    __shared__ u32 s_seg;
+    __shared__ i128 red[32];
+    const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    make_pattern_words(patw, A.k0);
+
+    for (;;) {
+        if (tid == 0) s_seg = atomicAdd(A.queue, 1u);
+        __syncthreads();
+        const u64 s = s_seg;
+        __syncthreads();
+        if (s >= A.nseg) break;
+        const u64 L = s * A.span;
+        fill_pattern(bits, seg_words, L, patw, A.k0);
+        __syncthreads();
+        const u64 end = L + A.span;
+        // cross off p_b, k0 < b <= B (the prime itself included)
+        auto none = [](u32) {};
+        u32 b = A.k0 + 1;
+        for (; b <= A.B; b++) {
+            const u64 p = A.primes[b];
+            if (p * 8 > A.seg_bytes) break;
+            u64 ks = L ? (L + p - 1) / p : 0;
+            if (ks < p) ks = p;
+            cross_off_coop(bits, A.seg_bytes, L, (u32)p, ks, tid, NT, none);
+        }
+        for (u32 bb = b + tid; bb <= A.B; bb += NT) {
+            const u64 p = A.primes[bb];
+            u64 ks = L ? (L + p - 1) / p : 0;
+            if (ks < p) ks = p;
+            cross_off_single(bits, A.seg_bytes, L, (u32)p, ks, none);
+        }
+        // the sieving primes themselves (only in the first segments)
+        for (u32 bb = A.k0 + 1 + tid; bb <= A.B; bb += NT) {
+            const u64 p = A.primes[bb];
+            if (p >= end) break;
+            if (p >= L) {
+                u32 pos = seg_pos(p, L);
+                atomicAnd(&bits[pos >> 5], ~(1u << (pos & 31)));
+            }
+        }
+        __syncthreads();
+        for (u32 k = tid; k < nblk; k += NT) {
+            u32 c = 0;
+            for (u32 w = 0; w < 32; w++) c += __popc(bits[32 * k + w]);
+            blk[k] = c;
+        }
+        __syncthreads();
+        // exclusive scan of the block counts
+        {
+            const u32 per = (nblk + NT - 1) / NT;
+            u32 b0 = tid * per, b1 = b0 + per < nblk ? b0 + per : nblk;
+            u32 loc = 0;
+            for (u32 k = b0; k < b1; k++) loc += blk[k];
+            u32 incl = loc;
+            for (int o = 1; o < 32; o <<= 1) {
+                u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) wsum[wid] = incl;
+            __syncthreads();
+            if (wid == 0) {
+                u32 w = lane < NT / 32 ? wsum[lane] : 0, wi = w;
+                for (int o = 1; o < 32; o <<= 1) {
+                    u32 v = __shfl_up_sync(0xffffffffu, wi, o);
+                    if (lane >= o) wi += v;
+                }
+                if (lane < NT / 32) wsum[lane] = wi - w;
+            }
+            __syncthreads();
+            u32 run = wsum[wid] + incl - loc;
+            for (u32 k = b0; k < b1; k++) {
+                pre[k] = run;
+                run += blk[k];
+            }
+            if (tid == NT - 1) pre[nblk] = run;
+        }
+        __syncthreads();
+        // the p with x/p in [L, end): p in (x/end, x/L], y < p <= r
+        u64 plo = pc_max(A.x / end, A.y);       // exclusive
+        u64 phi = L ? pc_min(A.x / L, A.r) : A.r;
+        i64 acc = 0;
+        u32 tl = 0;
+        if (phi > plo) {
+            const u64 w0 = (plo + 1) / 240, w1 = phi / 240;
+            for (u64 w = w0 + tid; w <= w1; w += NT) {
+                u64 v = __ldg(A.pit.words + w);
+                while (v) {
+                    int bi = __ffsll((long long)v) - 1;
+                    v &= v - 1;
+                    u64 p = 240 * w + 30 * (u64)(bi >> 3) + c_R8[bi & 7];
+                    if (p <= plo || p > phi) continue;
+                    u64 q = A.x / p;
+                    u32 e = seg_count_end(q, L);
+                    u32 eb = e >> 10, ew = e >> 6;
+                    u32 c = pre[eb];
+                    for (u32 ww = eb << 4; ww < ew; ww++) c += __popcll(bits64[ww]);
+                    if (e & 63) c += __popcll(bits64[ew] & ((1ull << (e & 63)) - 1));
+                    acc += c;
+                    tl++;
+                }
+            }
+        }
+        for (int o = 16; o; o >>= 1) tl += __shfl_xor_sync(0xffffffffu, tl, o);
+        __syncthreads();
+        if (lane == 0) wsum[wid] = tl;
+        __syncthreads();
+        i128 tot = block_sum_i128((i128)acc, red);
+        if (tid == 0) {
+            u32 t = 0;
+            for (u32 w = 0; w < NT / 32; w++) t += wsum[w];
+            A.tally[s] = t;
+            A.cnt[s] = pre[nblk];
+            store_i128(A.acc + s, tot);
+        }
+    }
+}
+
+// sum_s acc[s] + tally[s] * phi(L_s - 1, B), phi(L_s - 1, B) = sum_{s'<s} cnt[s']
+__global__ void p2_combine_kernel(P2Args A, I128Pair* out)
+{
+    __shared__ u64 wsum[32];
+    __shared__ u64 s_carry;
+    __shared__ i128 red[32];
+    const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NT = blockDim.x;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    i128 dot = 0;
+    for (u64 base = 0; base < A.nseg; base += NT) {
+        const u64 s = base + threadIdx.x;
+        const u64 v = s < A.nseg ? A.cnt[s] : 0;
+        u64 incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            u64 t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            u64 w = lane < NT / 32 ? wsum[lane] : 0, wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                u64 t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            if (lane < NT / 32) wsum[lane] = wi - w;
+        }
+        __syncthreads();
+        const u64 c0 = s_carry;
+        const u64 carry = c0 + wsum[wid] + incl - v;
+        if (s < A.nseg) dot += load_i128(A.acc + s) + (i128)A.tally[s] * (i128)carry;
+        __syncthreads();
+        if (threadIdx.x == NT - 1) s_carry = c0 + wsum[wid] + incl;
+        __syncthreads();
+    }
+    dot = block_sum_i128(dot, red);
+    if (threadIdx.x == 0) store_i128(out, load_i128(out) + dot);
+}
+
+// tiny z (fewer than 3 sieving primes): every pi(x/p) straight from the pi table
+__global__ void p2_lookup_kernel(u64 x, u64 y, u64 r, PiTable pit, I128Pair* out)
+{
+    __shared__ i128 red[32];
+    i128 s = 0;
+    for (u64 p = y + 1 + threadIdx.x; p <= r; p += blockDim.x) {
+        u64 pp = pi_lookup(pit, p);
+        if (pp == pi_lookup(pit, p - 1)) continue;   // p not prime
+        s += (i128)pi_lookup(pit, x / p) - (i128)pp + 1;
+    }
+    s = block_sum_i128(s, red);
+    if (threadIdx.x == 0) store_i128(out, load_i128(out) + s);
+}
+
+int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
+{
+    const u64 r = pc_isqrt(x);
+    if (r <= y) return PC_OK;
+    const u64 z = x / y;
+    u64 vals[3] = {r, pc_isqrt(z), 0};
+    u64 pv[3];
+    PC_TRY(tables_pi_values(ctx, vals, pv, 2));
+    const u64 K = pv[0], B = pv[1];
+    if (K <= a) return PC_OK;
+    if (B < 3) {
+        p2_lookup_kernel<<<1, 256, 0, ctx->stream>>>(x, y, r, ctx->T.pi(), out);
+        PC_LAUNCHED(ctx);
+        ctx->stats.kernel_launches++;
+        return PC_OK;
+    }
+    P2Args A{};
+    A.x = x;
+    A.y = y;
+    A.z = z;
+    A.r = r;
+    A.B = (u32)B;
+    A.k0 = B >= 5 ? 5 : (u32)B;
+    A.seg_bytes = pc_seg_bytes(ctx);
+    A.span = 30ull * A.seg_bytes;
+    A.nseg = z / A.span + 1;
+    A.pit = ctx->T.pi();
+    A.primes = ctx->T.primes.as<u32>();
+    PC_TRY(buf_reserve(ctx, ctx->counts, A.nseg * 2 * sizeof(u32)));
+    PC_TRY(buf_reserve(ctx, ctx->acc_seg, A.nseg * sizeof(I128Pair)));
+    PC_TRY(buf_reserve(ctx, ctx->queue, 64));
+    PC_CUDA(ctx, cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream));
+    A.cnt = ctx->counts.as<u32>();
+    A.tally = A.cnt + A.nseg;
+    A.acc = ctx->acc_seg.as<I128Pair>();
+    A.queue = ctx->queue.as<u32>();
+    const u32 nblk = A.seg_bytes >> 7;
+    size_t smem = A.seg_bytes + (2 * (size_t)nblk + 2) * sizeof(u32);
+    cudaError_t e = cudaFuncSetAttribute(p2_sieve_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        pc_set_error(ctx, "p2 smem attribute: %s", cudaGetErrorString(e));
+        return PC_ECUDA;
+    }
+    int per_sm = (int)(ctx->smem_optin / (smem + 4096));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 4) per_sm = 4;
+    int ctas = ctx->sm_count * per_sm;
+    if ((u64)ctas > A.nseg) ctas = (int)A.nseg;
+    p2_sieve_kernel<512><<<ctas, 512, smem, ctx->stream>>>(A);
+    PC_LAUNCHED(ctx);
+    p2_combine_kernel<<<1, 1024, 0, ctx->stream>>>(A, out);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches += 2;
+    return PC_OK;
+}
+
+// constant part of P2: (K - a)(B - 1) - sum_{k=a+1}^{K} (k - 1), with the
+// same K = pi(isqrt x), B = pi(isqrt z) as run_p2 (host, exact)
+int p2_constant(pc_ctx* ctx, u64 x, u64 y, u64 a, i128* out)
+{
+    const u64 r = pc_isqrt(x);
+    *out = 0;
+    if (r <= y) return PC_OK;
+    const u64 z = x / y;
+    u64 vals[2] = {r, pc_isqrt(z)};
+    u64 pv[2];
+    PC_TRY(tables_pi_values(ctx, vals, pv, 2));
+    const u64 K = pv[0], B = pv[1];
+    if (K <= a || B < 3) return PC_OK;
+    i128 n = (i128)(K - a);
+    i128 sum_k1 = ((i128)K * (i128)(K - 1) - (i128)a * (i128)(a - (a ? 1 : 0))) / 2;   // sum_{k=a+1}^{K} (k-1)
+    *out = n * (i128)(B - 1) - sum_k1;
+    return PC_OK;
+}

@@ -1,0 +1,467 @@
+// pc_tables.cu -- device table builders (all on the GPU).
+//
+//  * bootstrap primes <= 65536
+//  * pi table: mod-30 prime bitset over [0, pi_limit] plus per-word prefix
+//    counts, giving pi(v) in O(1) (the role of the pi(y) table of Section 2;
+//    the popcount bitset is this library's GPU form of Section 2.1's idea of
+//    a sampled table completed by a short local count)
+//  * primes p_1..p_n as a dense array (Section 2: table of primes p_b)
+//  * the squarefree m-list with lpf / mu / gpf (Section 2.2: the p_min(y)
+//    and mu(y) data the leaf sums iterate over), plus a rank bitset giving
+//    the list index of any m in O(1)
+//  * phi(., c) residue tables for the primorial of c (the wheel of Section 4)
+#include "pc_internal.h"
+#include "pc_sieve.cuh"
+
+
+// ------------------------------------------------------ bootstrap primes
+__global__ void small_primes_kernel(u32* out, u32* count)
+{
+    // thread t owns the 64 integers [64t, 64t+64) of [0, 65536)
+
+    __shared__ u32 wsum[32];
+    const u32 t = threadIdx.x;
+    u64 mask = 0;
+    for (u32 i = 0; i < 64; i++) {
+        u32 n = 64 * t + i;
+        bool pr = n >= 2;
+        for (u32 d = 2; pr && d * d <= n; d++)
+            if (n % d == 0) pr = false;
+        if (pr) mask |= 1ull << i;
+    }
+    u32 c = __popcll(mask);
+    // block exclusive scan of c
+    u32 lane = t & 31, wid = t >> 5;
+    u32 incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        u32 w = wsum[lane], wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            u32 v = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += v;
+        }
+        wsum[lane] = wi - w;
+        if (lane == 31) *count = wi;
+    }
+    __syncthreads();
+    u32 pos = wsum[wid] + incl - c;
+
+    while (mask) {
+        int i = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
+        out[pos++] = 64 * t + (u32)i;
+    }
+}
+
+// ------------------------------------------------------------- pi table
+// One CTA per segment of PI_SEG_BYTES bytes: cross off multiples k*p,
+// k >= p (primes stay set), then write the words and their popcounts.
+static constexpr u32 PI_SEG_BYTES = 16384;
+
+__global__ void pi_sieve_kernel(const u32* sp, u32 nsp, u64 limit, u64 nwords64, u64* words, u32* wcnt)
+{
+    __shared__ u32 bits[PI_SEG_BYTES / 4];
+    const u64 L = (u64)blockIdx.x * (30ull * PI_SEG_BYTES);
+    const u64 end = L + 30ull * PI_SEG_BYTES;   // exclusive
+    for (u32 w = threadIdx.x; w < PI_SEG_BYTES / 4; w += blockDim.x) bits[w] = 0xFFFFFFFFu;
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) bits[0] &= ~1u;   // 1 is not prime
+    __syncthreads();
+    u64 hi = end - 1 < limit ? end - 1 : limit;
+    u64 r = pc_isqrt(hi);
+    auto none = [](u32) {};
+    // primes 7.. (sp[0..2] = 2, 3, 5)
+    for (u32 i = 3; i < nsp; i++) {
+        u32 p = sp[i];
+        if (p > r) break;
+        u64 kstart = (L + p - 1) / p;
+        if (kstart < p) kstart = p;
+        if ((u64)p * 8 <= PI_SEG_BYTES) {
+            cross_off_coop(bits, PI_SEG_BYTES, L, p, kstart, threadIdx.x, blockDim.x, none);
+        } else if (threadIdx.x < 32) {
+            cross_off_coop(bits, PI_SEG_BYTES, L, p, kstart, threadIdx.x, 32, none);
+        }
+    }
+    __syncthreads();
+    const u64* b64 = (const u64*)bits;
+    u64 w0 = (u64)blockIdx.x * (PI_SEG_BYTES / 8);
+    for (u32 w = threadIdx.x; w < PI_SEG_BYTES / 8; w += blockDim.x) {
+        u64 gw = w0 + w;
+        if (gw < nwords64) {
+            u64 v = b64[w];
+            words[gw] = v;
+            wcnt[gw] = __popcll(v);
+        }
+    }
+}
+
+// ------------------------------------------------------------- primes[]
+// primes[k] = p_k for 1 <= k <= n_out; primes[0] = 1.
+__global__ void extract_primes_kernel(const u64* words, const u32* pcnt, u64 nwords, u32* primes, u64 n_out)
+{
+    u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w == 0) {
+        primes[0] = 1;
+        if (n_out >= 1) primes[1] = 2;
+        if (n_out >= 2) primes[2] = 3;
+        if (n_out >= 3) primes[3] = 5;
+    }
+    if (w >= nwords) return;
+    u64 v = words[w];
+    u64 idx = 3 + pcnt[w];
+    while (v) {
+        int b = __ffsll((long long)v) - 1;
+        v &= v - 1;
+        idx++;
+        if (idx > n_out) return;
+        u64 n = 240 * w + 30 * (u64)(b >> 3) + c_R8[b & 7];
+        primes[idx] = (u32)n;
+    }
+}
+
+// --------------------------------------------------------------- m-list
+// One CTA per ML_CHUNK integers [lo, lo + ML_CHUNK).  Every prime p <= sqrt(Y)
+// is applied to its multiples with shared-memory atomics (order free):
+// lpf = min, largest small factor = max, parity of the number of small
+// factors, product of small factors, and a square-factor flag.  What is left
+// after dividing out the small factors is 1 or one prime > sqrt(Y).
+static constexpr u32 ML_CHUNK = 2048;
+
+__global__ void mlist_kernel(const u32* sp, u32 nsp, u64 Y, u32 pcmin, PiTable pit,
+                             u64* info_tmp, u64* rbits)
+{
+    __shared__ u32 prod[ML_CHUNK];
+    __shared__ u32 lpf[ML_CHUNK];
+    __shared__ u32 gsm[ML_CHUNK];
+    __shared__ u32 flg[ML_CHUNK];
+    const u64 lo = (u64)blockIdx.x * ML_CHUNK;
+    for (u32 i = threadIdx.x; i < ML_CHUNK; i += blockDim.x) {
+        prod[i] = 1;
+        lpf[i] = 0xFFFFFFFFu;
+        gsm[i] = 0;
+        flg[i] = 0;
+    }
+    __syncthreads();
+    u64 hi = lo + ML_CHUNK - 1 < Y ? lo + ML_CHUNK - 1 : Y;
+    u32 r = (u32)pc_isqrt(Y);
+    // primes with many multiples: all threads per prime
+    u32 i = 0;
+    for (; i < nsp; i++) {
+        u32 p = sp[i];
+        if (p > r || p * 8 > ML_CHUNK) break;
+        u64 first = (lo + p - 1) / p * p;
+        if (first < p) first = p;
+        for (u64 n = first + (u64)threadIdx.x * p; n <= hi; n += (u64)blockDim.x * p) {
+            u32 k = (u32)(n - lo);
+            u64 q = n / p;
+            if (q % p == 0) atomicOr(&flg[k], 2u);
+            atomicMin(&lpf[k], p);
+            atomicMax(&gsm[k], p);
+            atomicXor(&flg[k], 1u);
+            u32 cur = prod[k], seen;
+            do {
+                seen = cur;
+                cur = atomicCAS(&prod[k], seen, seen * p);
+            } while (cur != seen);
+        }
+    }
+    // primes with few multiples: one thread per prime
+    for (u32 j = i + threadIdx.x; j < nsp; j += blockDim.x) {
+        u32 p = sp[j];
+        if (p > r) break;
+        u64 first = (lo + p - 1) / p * p;
+        if (first < p) first = p;
+        for (u64 n = first; n <= hi; n += p) {
+            u32 k = (u32)(n - lo);
+            u64 q = n / p;
+            if (q % p == 0) atomicOr(&flg[k], 2u);
+            atomicMin(&lpf[k], p);
+            atomicMax(&gsm[k], p);
+            atomicXor(&flg[k], 1u);
+            u32 cur = prod[k], seen;
+            do {
+                seen = cur;
+                cur = atomicCAS(&prod[k], seen, seen * p);
+            } while (cur != seen);
+        }
+    }
+    __syncthreads();
+    // finalize: one thread per integer, 64 integers per rank word
+    for (u32 k = threadIdx.x; k < ML_CHUNK; k += blockDim.x) {
+        u64 n = lo + k;
+        bool entry = false;
+        u64 packed = 0;
+        if (n >= 2 && n <= Y && !(flg[k] & 2u)) {
+            u32 par = flg[k] & 1u;
+            u64 l = lpf[k], g = gsm[k];
+            u64 big = n / prod[k];
+            if (big > 1) {
+                par ^= 1u;
+                g = big;
+                if (big < l) l = big;
+            }
+            if (l > pcmin) {
+                entry = true;
+                u64 li = pi_lookup(pit, l), gi = pi_lookup(pit, g);
+                packed = (li << 1) | (u64)par | (gi << 32);
+            }
+        }
+        if (n <= Y) info_tmp[n] = packed;
+        unsigned bal = __ballot_sync(0xffffffffu, entry);
+        // two warps-worth of 32 integers make one 64-bit rank word
+        if ((k & 31) == 0) {
+            u64 word_idx = n >> 6;
+            u32 half = (u32)(n >> 5) & 1u;
+            if (n <= Y) atomicOr((unsigned long long*)&rbits[word_idx], (u64)bal << (32 * half));
+        }
+    }
+}
+
+__global__ void popc_words_kernel(const u64* w, u64 n, u32* out)
+{
+    u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __popcll(w[i]);
+}
+
+__global__ void mlist_scatter_kernel(const u64* info_tmp, const u64* rbits, const u32* rcnt, u64 Y,
+                                     u32* mm, u32* minfo, u32* mgpf)
+{
+    u64 n = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n > Y) return;
+    u64 w = rbits[n >> 6];
+    u32 b = (u32)(n & 63);
+    if (!((w >> b) & 1)) return;
+    u64 idx = rcnt[n >> 6] + __popcll(w & ((1ull << b) - 1));
+    u64 packed = info_tmp[n];
+    mm[idx] = (u32)n;
+    minfo[idx] = (u32)packed;          // (lpf_index << 1) | parity
+    mgpf[idx] = (u32)(packed >> 32);
+}
+
+// ------------------------------------------------------------ phi tables
+__global__ void coprime_flags_kernel(u32 Q, u32 c, const u32* sp, u32* flags)
+{
+    u32 r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= Q) return;
+    u32 f = r >= 1;
+    for (u32 i = 0; i < c; i++)
+        if (r % sp[i] == 0) f = 0;
+    flags[r] = f;
+}
+
+// ------------------------------------------------------------------ host
+static int ensure_small(pc_ctx* ctx)
+{
+    Tables& T = ctx->T;
+    if (T.n_small) return PC_OK;
+    PC_TRY(buf_reserve(ctx, T.small_primes, 8192 * sizeof(u32)));
+    PC_TRY(buf_reserve(ctx, ctx->misc, 64));
+    small_primes_kernel<<<1, 1024, 0, ctx->stream>>>(T.small_primes.as<u32>(), ctx->misc.as<u32>());
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    u32 n = 0;
+    PC_TRY(copy_to_host(ctx, &n, ctx->misc.p, sizeof(u32)));
+    T.n_small = n;
+    return PC_OK;
+}
+
+static int build_pi(pc_ctx* ctx, u64 limit)
+{
+    Tables& T = ctx->T;
+    u64 nwords = limit / 240 + 1;
+    u64 nseg = (limit + 30ull * PI_SEG_BYTES) / (30ull * PI_SEG_BYTES);
+    u64 nw_alloc = nseg * (PI_SEG_BYTES / 8);
+    PC_TRY(buf_reserve(ctx, T.pi_words, nw_alloc * sizeof(u64)));
+    PC_TRY(buf_reserve(ctx, T.pi_pcnt, (nw_alloc + 1) * sizeof(u32)));
+    PC_TRY(buf_reserve(ctx, ctx->scan_tmp, 16));
+    DevBuf tmp;
+    int rc = buf_reserve(ctx, tmp, (nwords + 1) * sizeof(u32));
+    if (rc) return rc;
+    pi_sieve_kernel<<<(unsigned)nseg, 256, 0, ctx->stream>>>(T.small_primes.as<u32>(), T.n_small, limit, nwords,
+                                                            T.pi_words.as<u64>(), tmp.as<u32>());
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) rc = scan_exclusive_u32_to_u32(ctx, tmp.as<u32>(), T.pi_pcnt.as<u32>(), nwords);
+    else {
+        pc_set_error(ctx, "pi_sieve_kernel launch: %s", cudaGetErrorString(e));
+        rc = PC_ECUDA;
+    }
+    if (rc == PC_OK) {
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            pc_set_error(ctx, "pi table build: %s", cudaGetErrorString(e));
+            rc = PC_ECUDA;
+        }
+    }
+    buf_free(tmp);
+    ctx->stats.kernel_launches++;
+    if (rc == PC_OK) T.pi_limit = limit;
+    return rc;
+}
+
+static int build_primes(pc_ctx* ctx, u64 prime_limit)
+{
+    Tables& T = ctx->T;
+    // pi(prime_limit) and one sentinel prime above it (gap < 2048 below 2^64)
+    u64 v[1] = {prime_limit};
+    u64 np = 0;
+    PC_TRY(tables_pi_values(ctx, v, &np, 1));
+    u64 n_out = np + 1;
+    PC_TRY(buf_reserve(ctx, T.primes, (n_out + 2) * sizeof(u32)));
+    u64 wlim = (prime_limit + 2048) / 240 + 1;
+    u64 wmax = T.pi_limit / 240 + 1;
+    if (wlim > wmax) wlim = wmax;
+    extract_primes_kernel<<<(unsigned)((wlim + 255) / 256), 256, 0, ctx->stream>>>(
+        T.pi_words.as<u64>(), T.pi_pcnt.as<u32>(), wlim, T.primes.as<u32>(), n_out);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    T.nprimes = np;
+    T.prime_limit = prime_limit;
+    return PC_OK;
+}
+
+static int build_mlist(pc_ctx* ctx, u64 Y, u32 cmin)
+{
+    Tables& T = ctx->T;
+    u32 pcmin = 1;   // lpf must exceed p_cmin (p_0 = 1)
+    {
+        static const u32 P8[8] = {1, 2, 3, 5, 7, 11, 13, 17};
+        pcmin = P8[cmin];
+    }
+    u64 nrw = Y / 64 + 1;
+    DevBuf info_tmp;
+    int rc = buf_reserve(ctx, info_tmp, (Y + 1) * sizeof(u64));
+    if (rc) return rc;
+    PC_TRY(buf_reserve(ctx, T.rank_bits, nrw * sizeof(u64)));
+    PC_TRY(buf_reserve(ctx, T.rank_cnt, (nrw + 1) * sizeof(u32)));
+    PC_CUDA(ctx, cudaMemsetAsync(T.rank_bits.p, 0, nrw * sizeof(u64), ctx->stream));
+    u64 nchunks = Y / ML_CHUNK + 1;
+    mlist_kernel<<<(unsigned)nchunks, 256, 0, ctx->stream>>>(T.small_primes.as<u32>(), T.n_small, Y, pcmin,
+                                                             T.pi(), info_tmp.as<u64>(), T.rank_bits.as<u64>());
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        buf_free(info_tmp);
+        pc_set_error(ctx, "mlist_kernel launch: %s", cudaGetErrorString(e));
+        return PC_ECUDA;
+    }
+    DevBuf tmp;
+    rc = buf_reserve(ctx, tmp, (nrw + 1) * sizeof(u32));
+    if (rc) { buf_free(info_tmp); return rc; }
+    popc_words_kernel<<<(unsigned)((nrw + 255) / 256), 256, 0, ctx->stream>>>(T.rank_bits.as<u64>(), nrw, tmp.as<u32>());
+    rc = scan_exclusive_u32_to_u32(ctx, tmp.as<u32>(), T.rank_cnt.as<u32>(), nrw);
+    u32 total = 0;
+    if (rc == PC_OK) rc = copy_to_host(ctx, &total, T.rank_cnt.as<u32>() + nrw, sizeof(u32));
+    if (rc == PC_OK) rc = buf_reserve(ctx, T.ml_m, ((u64)total + 1) * sizeof(u32));
+    if (rc == PC_OK) rc = buf_reserve(ctx, T.ml_info, ((u64)total + 1) * sizeof(u32));
+    if (rc == PC_OK) rc = buf_reserve(ctx, T.ml_gpf, ((u64)total + 1) * sizeof(u32));
+    if (rc == PC_OK) {
+        mlist_scatter_kernel<<<(unsigned)((Y + 256) / 256), 256, 0, ctx->stream>>>(
+            info_tmp.as<u64>(), T.rank_bits.as<u64>(), T.rank_cnt.as<u32>(), Y, T.ml_m.as<u32>(),
+            T.ml_info.as<u32>(), T.ml_gpf.as<u32>());
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            pc_set_error(ctx, "m-list build: %s", cudaGetErrorString(e));
+            rc = PC_ECUDA;
+        }
+    }
+    buf_free(tmp);
+    buf_free(info_tmp);
+    ctx->stats.kernel_launches += 3;
+    if (rc == PC_OK) {
+        T.ml_limit = Y;
+        T.ml_cmin = cmin;
+        T.ml_n = total;
+    }
+    return rc;
+}
+
+int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 cmin)
+{
+    Tables& T = ctx->T;
+    PC_TRY(ensure_small(ctx));
+    if (prime_limit < 64) prime_limit = 64;
+    if (pi_limit < prime_limit + 2048) pi_limit = prime_limit + 2048;
+    if (pi_limit < 65536) pi_limit = 65536;
+    bool new_pi = false;
+    if (pi_limit > T.pi_limit) {
+        // grow geometrically so that a rising sequence of queries rebuilds rarely
+        u64 lim = pi_limit;
+        if (T.pi_limit && lim < T.pi_limit + T.pi_limit / 2) lim = T.pi_limit + T.pi_limit / 2;
+        PC_TRY(build_pi(ctx, lim));
+        new_pi = true;
+    }
+    if (new_pi || prime_limit > T.prime_limit) {
+        u64 lim = prime_limit;
+        if (T.prime_limit && lim < T.prime_limit + T.prime_limit / 2) lim = T.prime_limit + T.prime_limit / 2;
+        if (lim + 2048 > T.pi_limit) lim = T.pi_limit - 2048;
+        if (lim < prime_limit) lim = prime_limit;
+        PC_TRY(build_primes(ctx, lim));
+    }
+    if (ml_limit > 0 && (ml_limit > T.ml_limit || cmin < T.ml_cmin)) {
+        u64 lim = ml_limit;
+        if (T.ml_limit && lim < T.ml_limit + T.ml_limit / 2 && cmin >= T.ml_cmin) lim = T.ml_limit + T.ml_limit / 2;
+        if (lim > T.pi_limit) lim = T.pi_limit;
+        if (lim < ml_limit) lim = ml_limit;
+        u32 cm = cmin < T.ml_cmin ? cmin : T.ml_cmin;
+        if (T.ml_limit == 0) cm = cmin;
+        PC_TRY(build_mlist(ctx, lim, cm));
+    }
+    return PC_OK;
+}
+
+__global__ void pi_values_kernel(PiTable t, const u64* v, u64* out, int n)
+{
+    int i = threadIdx.x;
+    if (i < n) out[i] = pi_lookup(t, v[i]);
+}
+
+int tables_pi_values(pc_ctx* ctx, const u64* v, u64* out, int n)
+{
+    if (n > 32) return PC_EINVAL;
+    for (int i = 0; i < n; i++)
+        if (v[i] > ctx->T.pi_limit) {
+            pc_set_error(ctx, "pi lookup %llu beyond table %llu", (unsigned long long)v[i],
+                         (unsigned long long)ctx->T.pi_limit);
+            return PC_EINVAL;
+        }
+    PC_TRY(buf_reserve(ctx, ctx->misc, 64 * sizeof(u64)));
+    u64* d = ctx->misc.as<u64>();
+    PC_CUDA(ctx, cudaMemcpyAsync(d, v, n * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
+    pi_values_kernel<<<1, 32, 0, ctx->stream>>>(ctx->T.pi(), d, d + 32, n);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    return copy_to_host(ctx, out, d + 32, n * sizeof(u64));
+}
+
+int tables_phi_c(pc_ctx* ctx, u32 c)
+{
+    Tables& T = ctx->T;
+    if (c == 0 || T.phiT_ok[c]) return PC_OK;
+    PC_TRY(ensure_small(ctx));
+    u32 Q = 1;
+    static const u32 P8[8] = {1, 2, 3, 5, 7, 11, 13, 17};
+    for (u32 i = 1; i <= c; i++) Q *= P8[i];
+    DevBuf flags;
+    PC_TRY(buf_reserve(ctx, flags, (Q + 1) * sizeof(u32)));
+    int rc = buf_reserve(ctx, T.phiT[c], (Q + 1) * sizeof(u32));
+    if (rc == PC_OK) {
+        coprime_flags_kernel<<<(Q + 255) / 256, 256, 0, ctx->stream>>>(Q, c, T.small_primes.as<u32>(), flags.as<u32>());
+        rc = scan_exclusive_u32_to_u32(ctx, flags.as<u32>(), T.phiT[c].as<u32>(), Q);
+        if (rc == PC_OK) {
+            cudaError_t e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) {
+                pc_set_error(ctx, "phi table: %s", cudaGetErrorString(e));
+                rc = PC_ECUDA;
+            }
+        }
+    }
+    buf_free(flags);
+    ctx->stats.kernel_launches++;
+    if (rc == PC_OK) T.phiT_ok[c] = true;
+    return rc;
+}

@@ -1,0 +1,183 @@
+"""GPU parity: every part of the CUDA path against the CPU oracle, through
+the C ABI, bit for bit (all quantities are exact integers)."""
+import math
+import random
+
+import pytest
+
+import oracle as o
+import paper_1503_01839_gb300 as pc
+from conftest import read_table
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx_small():
+    # 1 KiB segments = 30720 integers: small inputs still span many segments
+    with pc.Context(0, seg_bytes=1024, ctas_per_sm=4, threads=256) as c:
+        yield c
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    with pc.Context(0) as c:
+        yield c
+
+
+def y_for(x, alpha):
+    return min(alpha * o.iroot3(x), o.isqrt(x))
+
+
+CASES = [(10 ** 6, 1), (10 ** 6, 10), (3 * 10 ** 7, 2), (10 ** 9, 1), (10 ** 9, 5), (10 ** 10, 1),
+         (10 ** 10, 4), (2 ** 35, 3), (10 ** 11, 2), (10 ** 12, 1), (10 ** 12, 6)]
+
+
+@pytest.mark.parametrize("x,alpha", CASES)
+def test_leaf_sums_parity(ctx_small, ctx, x, alpha):
+    y = y_for(x, alpha)
+    for c in (0, 2, 3, 5, 7):
+        want = o.leaf_sums(x, y, c)
+        for cx in (ctx_small, ctx):
+            got = cx.leaf_sums(x, y, c)
+            for k in ("S1", "S2_triv", "S2_easy", "S2_hard", "P2"):
+                assert got[k] == want[k], (x, y, c, k, got[k], want[k])
+
+
+@pytest.mark.parametrize("x,alpha", CASES[:8])
+def test_s2_hard_parity(ctx_small, x, alpha):
+    y = y_for(x, alpha)
+    for c in range(0, 8):
+        want = o.leaf_sums(x, y, c)["S2_hard"]
+        assert ctx_small.s2_hard(x, y, c) == want, (x, y, c)
+
+
+def test_s2_hard_many_segment_sizes():
+    x, y, c = 10 ** 11, 4641 * 2, 5
+    want = o.leaf_sums(x, y, c)["S2_hard"]
+    for sb, cps, th in [(1024, 1, 128), (2048, 2, 256), (5120, 3, 512), (65536, 0, 512), (131072, 1, 1024),
+                        (196608, 1, 512)]:
+        with pc.Context(0, seg_bytes=sb, ctas_per_sm=cps, threads=th) as cx:
+            assert cx.s2_hard(x, y, c) == want, (sb, cps, th)
+
+
+def test_truncated_phi_parts(ctx_small):
+    # phi(x, a) = S1 + S2 with the tree truncated at p_a (gpf(m) <= p_a)
+    for x, y, a, c in [(10 ** 7, 300, 30, 5), (10 ** 9, 1000, 100, 5), (10 ** 9, 1000, 168, 3),
+                       (10 ** 10, 2154, 7, 2), (10 ** 10, 5000, 300, 5)]:
+        want = o.leaf_sums(x, y, c, a)
+        got = ctx_small.leaf_sums(x, y, c, a)
+        for k in ("S1", "S2_triv", "S2_easy", "S2_hard"):
+            assert got[k] == want[k], (x, y, a, c, k)
+
+
+def test_p2_parity(ctx_small, ctx):
+    for x, alpha in CASES:
+        y = y_for(x, alpha)
+        a = o.pi_sieve(y)
+        want = o.p2(x, a)
+        assert ctx_small.p2(x, y) == want
+        assert ctx.p2(x, y) == want
+
+
+def test_pi_count_table1(ctx, pi_pow10):
+    for n in range(1, 19):
+        assert ctx.pi_count(10 ** n) == pi_pow10[n], n
+
+
+def test_pi_count_table2(ctx, pi_pow2):
+    for m in range(1, 63):
+        assert ctx.pi_count(2 ** m) == pi_pow2[m], m
+
+
+def test_pi_count_alpha_segment_invariance(pi_pow10):
+    # Section 5: the same value with different (alpha, c, L)
+    x = 10 ** 14
+    for sb, alpha, c in [(1024, 1, 5), (8192, 3, 3), (65536, 8, 7), (196608, 20, 5), (32768, 40, 4)]:
+        with pc.Context(0, seg_bytes=sb, c=c) as cx:
+            assert cx.pi_count(x, alpha) == pi_pow10[14], (sb, alpha, c)
+
+
+def test_pi_count_small_x_exhaustive(ctx):
+    rng = random.Random(3)
+    xs = list(range(0, 200)) + [rng.randrange(200, 1 << 22) for _ in range(60)] + \
+        [(1 << 20) - 1, 1 << 20, (1 << 20) + 1]
+    for x in xs:
+        assert ctx.pi_count(x) == o.pi_sieve(x), x
+
+
+def test_pi_count_random_mid(ctx_small, ctx):
+    rng = random.Random(4)
+    for _ in range(12):
+        x = rng.randrange(1 << 21, 10 ** 10)
+        want = o.pi_meissel(x)
+        assert ctx.pi_count(x) == want, x
+        assert ctx_small.pi_count(x, rng.randrange(1, 8)) == want, x
+
+
+def test_phi_vs_oracle(ctx):
+    rng = random.Random(5)
+    for _ in range(40):
+        x = rng.randrange(0, 3 * 10 ** 6)
+        a = rng.randrange(0, 250)
+        assert ctx.phi(x, a) == o.phi_brute(x, a), (x, a)
+    for a in (10, 100, 1000):
+        assert ctx.phi(10 ** 12, a) == o.phi_rec(10 ** 12, a), a
+
+
+def test_phi_1e14_recurrence(ctx):
+    # Eq. (4.1) at full size: phi(x, a) = phi(x, a-1) - phi(x/p_a, a-1)
+    x = 10 ** 14
+    for a in (10, 100, 1000):
+        pa = o.nth_prime(a)
+        assert ctx.phi(x, a) == ctx.phi(x, a - 1) - ctx.phi(x // pa, a - 1), a
+
+
+def test_phi_legendre_branch(ctx, pi_pow10):
+    # a >= pi(isqrt x): phi(x, a) = pi(x) - a + 1 (Section 4)
+    x = 10 ** 12
+    a = o.pi_sieve(10 ** 6)
+    assert ctx.phi(x, a) == pi_pow10[12] - a + 1
+    assert ctx.phi(x, 10 ** 9) == 1
+
+
+def test_s2_hard_tiny_inputs(ctx_small):
+    for x in list(range(8, 400, 7)) + [1000, 4096, 10007, 65536]:
+        for y in sorted({o.iroot3(x), o.isqrt(x)}):
+            a = o.pi_sieve(y)
+            for c in range(0, min(7, a) + 1):
+                assert ctx_small.s2_hard(x, y, c) == o.leaf_sums(x, y, c)["S2_hard"], (x, y, c)
+
+
+def test_errors(ctx):
+    with pytest.raises(pc.PicountError) as e:
+        ctx.pi_count(1 << 63)
+    assert e.value.code == -2
+    with pytest.raises(pc.PicountError) as e:
+        ctx.s2_hard(10 ** 10, 10, 5)       # y < iroot3(x)
+    assert e.value.code == -1
+    with pytest.raises(pc.PicountError) as e:
+        ctx.s2_hard(10 ** 10, 2154, 8)     # c > 7
+    assert e.value.code == -1
+    # the context stays usable after an error
+    assert ctx.pi_count(10 ** 9) == 50847534
+
+
+def test_batch_matches_single(ctx):
+    rng = random.Random(6)
+    xs = [int(10 ** rng.uniform(3, 12)) for _ in range(40)]
+    got = ctx.pi_count_batch(xs)
+    assert got == [ctx.pi_count(x) for x in xs]
+
+
+def test_full_size_pins(pi_pow10, pi_pow2):
+    # the largest workloads, in the launch configuration the benchmark uses
+    with pc.Context(0) as cx:
+        assert cx.pi_count(10 ** 18, 20) == pi_pow10[18]
+        assert cx.pi_count(2 ** 59, 20) == pi_pow2[59]
+        # S2_hard at 1e18 cannot be brute-forced: it must not depend on the
+        # segment geometry
+        y = 20 * 10 ** 6
+        h = cx.s2_hard(10 ** 18, y, 5)
+    with pc.Context(0, seg_bytes=131072, ctas_per_sm=1) as cx:
+        assert cx.s2_hard(10 ** 18, y, 5) == h
