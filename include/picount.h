@@ -72,6 +72,7 @@ typedef struct pc_stats {
     uint64_t segments;      /* hard-leaf sieve segments */
     uint64_t steps;         /* (segment, prime) steps of the hard-leaf sieve */
     uint64_t hard_leaves;   /* hard special leaves resolved by the sieve */
+    uint64_t clears;        /* multiples crossed off by the hard-leaf sieve */
     uint64_t kernel_launches;
     double ms_tables, ms_s1, ms_trivial, ms_easy, ms_hard, ms_p2, ms_total;
     double ms_hard_sieve;   /* the segmented sieve kernel alone (CUDA events) */

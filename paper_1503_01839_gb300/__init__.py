@@ -37,6 +37,7 @@ class PcStats(ctypes.Structure):
     _fields_ = [("x", ctypes.c_uint64), ("y", ctypes.c_uint64), ("z", ctypes.c_uint64), ("a", ctypes.c_uint64),
                 ("B", ctypes.c_uint64), ("c", ctypes.c_uint32), ("seg_bytes", ctypes.c_uint32),
                 ("segments", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("hard_leaves", ctypes.c_uint64),
+                ("clears", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64),
                 ("ms_tables", ctypes.c_double), ("ms_s1", ctypes.c_double), ("ms_trivial", ctypes.c_double),
                 ("ms_easy", ctypes.c_double), ("ms_hard", ctypes.c_double), ("ms_p2", ctypes.c_double),

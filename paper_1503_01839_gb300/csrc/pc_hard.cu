@@ -49,7 +49,7 @@ struct HardArgs {
     i32* tallies;
     I128Pair* acc;
     u32* queue;
-    unsigned long long* nleaves;
+    unsigned long long* nleaves;   // [0] hard leaves, [1] multiples crossed off
 };
 
 struct StepInfo {
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(NT) hard_sieve_kernel(HardArgs A)
         s_dec[0] = s_dec[1] = 0;
         s_tally = 0;
     }
-    unsigned long long nleaves = 0;
+    unsigned long long nleaves = 0, nclears = 0;
 
     for (;;) {
         if (tid == 0) {
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(NT) hard_sieve_kernel(HardArgs A)
                     u32 dec = 0;
                     if (p < RECOUNT_P) {
                         auto none = [](u32) {};
-                        cross_off_coop(bits, A.seg_bytes, L, (u32)p, ks, tid, NT, none);
+                        nclears += cross_off_coop(bits, A.seg_bytes, L, (u32)p, ks, tid, NT, none);
                         if (tid == 0 && p >= L && p < L + A.span) {
                             u32 pos = seg_pos(p, L);
                             atomicAnd(&bits[pos >> 5], ~(1u << (pos & 31)));
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(NT) hard_sieve_kernel(HardArgs A)
                         };
                         const u64 rounds = A.seg_bytes / p + 2;
                         u32 nt = rounds * 8 >= NT ? NT : (u32)((rounds * 8 + 31) & ~31ull);
-                        if (tid < nt) cross_off_coop(bits, A.seg_bytes, L, (u32)p, ks, tid, nt, newly);
+                        if (tid < nt) nclears += cross_off_coop(bits, A.seg_bytes, L, (u32)p, ks, tid, nt, newly);
                         if (tid == 0 && p >= L && p < L + A.span) {
                             u32 pos = seg_pos(p, L);
                             u32 msk = 1u << (pos & 31);
@@ -284,8 +284,12 @@ __global__ void __launch_bounds__(NT) hard_sieve_kernel(HardArgs A)
         i128 tot = block_sum_i128((i128)acc, red);
         if (tid == 0) store_i128(A.acc + s, tot);
     }
-    for (int o = 16; o; o >>= 1) nleaves += __shfl_xor_sync(0xffffffffu, nleaves, o);
+    for (int o = 16; o; o >>= 1) {
+        nleaves += __shfl_xor_sync(0xffffffffu, nleaves, o);
+        nclears += __shfl_xor_sync(0xffffffffu, nclears, o);
+    }
     if (lane == 0 && nleaves) atomicAdd(A.nleaves, nleaves);
+    if (lane == 0 && nclears) atomicAdd(A.nleaves + 1, nclears);
 }
 
 // ---------------------------------------------------------- schedule
@@ -471,12 +475,13 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     PC_TRY(reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out));
     PC_TRY(reduce_i128(ctx, A.acc, A.nseg, out));
 
-    u64 nl = 0;
-    PC_TRY(copy_to_host(ctx, &nl, A.nleaves, sizeof(u64)));
+    u64 nl[2] = {0, 0};
+    PC_TRY(copy_to_host(ctx, nl, A.nleaves, 2 * sizeof(u64)));
     float ms = 0;
     PC_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
     ctx->stats.ms_hard_sieve = ms;
-    ctx->stats.hard_leaves += nl;
+    ctx->stats.hard_leaves += nl[0];
+    ctx->stats.clears += nl[1];
     ctx->stats.segments = A.nseg;
     ctx->stats.steps = total;
     ctx->stats.seg_bytes = A.seg_bytes;

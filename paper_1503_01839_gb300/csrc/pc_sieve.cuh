@@ -23,7 +23,7 @@ __device__ __forceinline__ u64 coprime30_at_or_after(u64 k0)
 // NEWLY(bitpos) is invoked for every bit that was set before this call
 // cleared it (bit position relative to the segment).
 template <class F>
-__device__ __forceinline__ void cross_off_coop(u32* bits, u32 seg_bytes, u64 L, u32 p, u64 kstart,
+__device__ __forceinline__ u32 cross_off_coop(u32* bits, u32 seg_bytes, u64 L, u32 p, u64 kstart,
                                                int t, int nt, F&& newly)
 {
     const int j = t & 7;
@@ -38,15 +38,18 @@ __device__ __forceinline__ void cross_off_coop(u32* bits, u32 seg_bytes, u64 L, 
     u64 q = q0 + o;
     if (30 * q + rj < kstart) q += rounds;
     u64 byte64 = (u64)p * q + pr / 30;
-    if (byte64 < Lb) return;               // cannot happen for kstart*p >= L
+    if (byte64 < Lb) return 0;             // cannot happen for kstart*p >= L
     byte64 -= Lb;
     const u64 step = (u64)p * rounds;
+    u32 n = 0;
     for (; byte64 < seg_bytes; byte64 += step) {
         u32 pos = ((u32)byte64 << 3) + bit;
         u32 mask = 1u << (pos & 31);
         u32 old = atomicAnd(&bits[pos >> 5], ~mask);
         if (old & mask) newly(pos);
+        n++;
     }
+    return n;   // multiples crossed off by this thread
 }
 
 // One thread crosses off all multiples k*p (k >= kstart, k coprime to 30)

@@ -138,7 +138,9 @@ def test_phi_legendre_branch(ctx, pi_pow10):
     x = 10 ** 12
     a = o.pi_sieve(10 ** 6)
     assert ctx.phi(x, a) == pi_pow10[12] - a + 1
-    assert ctx.phi(x, 10 ** 9) == 1
+    # p_a > x: only n = 1 is left
+    assert ctx.phi(x, 10 ** 11) == 1
+    assert ctx.phi(x, 10 ** 9) == pi_pow10[12] - 10 ** 9 + 1
 
 
 def test_s2_hard_tiny_inputs(ctx_small):
