@@ -128,6 +128,45 @@ int pc_leaf_sums(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, uint64_t a, pc
  * are built once for the largest query and shared by all of them. */
 int pc_pi_count_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint64_t* out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * P2 for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart to this entry point; it exists for library
+ * users, not for the method.  Some callers must not call cudaMalloc: a serving
+ * process whose device memory is carved up in advance by its own pool
+ * allocator (an allocation outside the pool could exceed the budget), or a
+ * latency-critical path that cannot afford the device-wide synchronization a
+ * cudaMalloc or cudaFree may trigger.  pc_p2_noalloc allocates nothing and
+ * needs no context: the caller passes the inputs and the output as device
+ * memory it already owns, and the per-segment scratch lives in one fixed
+ * array inside the library (PC_NOALLOC_MAX_SEGMENTS * 16 bytes + 256 bytes,
+ * 512 KiB), which every GPU that loads the library keeps until the process
+ * exits.
+ *
+ * Computes P2(x, a), a = pi(y), as pc_p2 does:
+ *   x, y       iroot3(x) <= y <= isqrt(x), x < 2^63 (PC_ERANGE otherwise);
+ *   primes     device array of the primes 2, 3, 5, ... in ascending order,
+ *              n_primes entries: every prime <= isqrt(x) and at least one
+ *              prime above it (so the array provably covers isqrt(x));
+ *   out        device uint64_t that receives P2; it receives UINT64_MAX if
+ *              the last entry of primes is not above isqrt(x);
+ *   stream     cudaStream_t (NULL = legacy default stream) of the current
+ *              device.
+ * The work is enqueued on `stream` and the call returns without waiting; *out
+ * is valid once the stream reaches that point.  Size limit: z = x / y must
+ * give z / PC_NOALLOC_SEG_SPAN + 1 <= PC_NOALLOC_MAX_SEGMENTS segments
+ * (z < 3.2e10) and z >= 25; larger or smaller problems return PC_EINVAL and
+ * leave *out untouched.  The first call on a device looks up the scratch
+ * array's device address once (cudaGetSymbolAddress); make that first call
+ * before any stream capture begins.  All calls on a device share the one
+ * scratch array: calls that overlap on the GPU (concurrent streams, or host
+ * threads racing) race on it and give wrong results -- order them on one
+ * stream.  Each call clears the part of the scratch that must start at zero.
+ */
+#define PC_NOALLOC_MAX_SEGMENTS 32768
+#define PC_NOALLOC_SEG_SPAN 983040   /* integers per segment (32 KiB, mod-30 wheel) */
+int pc_p2_noalloc(uint64_t x, uint64_t y, const uint32_t* primes, uint64_t n_primes, uint64_t* out, void* stream);
+
 /* Counters of the last successful call. */
 int pc_last_stats(pc_ctx* ctx, pc_stats* out);
 

@@ -18,7 +18,8 @@ ERRORS = {-1: "PC_EINVAL", -2: "PC_ERANGE", -3: "PC_ENOMEM", -4: "PC_ECUDA", -5:
 
 # every symbol declared in include/picount.h
 SYMBOLS = ["pc_create", "pc_destroy", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
-           "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats", "pc_strerror", "pc_last_error", "pc_version"]
+           "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats", "pc_strerror", "pc_last_error", "pc_version",
+           "pc_p2_noalloc"]
 
 
 class PcI128(ctypes.Structure):
@@ -77,6 +78,8 @@ def lib():
             L.pc_last_error.argtypes = [p]
             L.pc_last_error.restype = ctypes.c_char_p
             L.pc_version.restype = ctypes.c_char_p
+            L.pc_p2_noalloc.argtypes = [u64, u64, p, u64, p, p]
+            L.pc_p2_noalloc.restype = ctypes.c_int
             for name in ("pc_create", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
                          "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats"):
                 getattr(L, name).restype = ctypes.c_int
@@ -171,6 +174,16 @@ class Context:
         s = PcStats()
         self._check(self._L.pc_last_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+
+def p2_noalloc(x: int, y: int, primes_ptr: int, n_primes: int, out_ptr: int, stream_handle: int = 0) -> None:
+    """P2(x, pi(y)) into the device uint64 at out_ptr, with no device
+    allocation: primes_ptr is a caller-owned device array of the primes
+    up to isqrt(x) (uint32, ascending).  Enqueued on stream_handle."""
+    rc = lib().pc_p2_noalloc(x, y, ctypes.c_void_p(primes_ptr), n_primes, ctypes.c_void_p(out_ptr),
+                             ctypes.c_void_p(stream_handle or 0))
+    if rc != PC_OK:
+        raise PicountError(rc, "pc_p2_noalloc rejected its arguments")
 
 
 def version() -> str:
