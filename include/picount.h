@@ -52,11 +52,12 @@ typedef struct pc_i128 {
 /* Tuning parameters; zero selects the built-in default of each field.
  * None of them changes any result. */
 typedef struct pc_params {
-    uint32_t seg_bytes;   /* bytes of shared-memory bitset per sieve segment
-                             (multiple of 1024, 1024..196608); one byte holds
-                             30 consecutive integers (mod-30 wheel) */
+    uint32_t seg_bytes;   /* bytes of shared-memory bitset per sieve segment:
+                             1024, 2048, or a multiple of 4096 up to 65536;
+                             one byte holds 30 consecutive integers (mod-30
+                             wheel); one warp per 4096 bytes */
     uint32_t ctas_per_sm; /* resident sieve CTAs per SM (1..4) */
-    uint32_t threads;     /* threads per sieve CTA (128..1024, multiple of 32) */
+    uint32_t threads;     /* reserved (the sieve uses one warp per 4 KiB) */
     uint32_t alpha;       /* default alpha of pc_pi_count (y = alpha*iroot3(x)) */
     uint32_t c;           /* default wheel depth c of pc_pi_count (0..7) */
     uint32_t reserved[3];

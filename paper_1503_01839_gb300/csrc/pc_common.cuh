@@ -15,6 +15,8 @@ typedef unsigned long long u64;
 typedef long long i64;
 typedef unsigned int u32;
 typedef int i32;
+typedef unsigned short u16;
+typedef unsigned char u8;
 typedef __int128 i128;
 typedef unsigned __int128 u128;
 
@@ -67,6 +69,23 @@ PC_HD u64 pc_iroot3(u64 n)
 }
 
 PC_HD u64 pc_min(u64 a, u64 b) { return a < b ? a : b; }
+
+// Division by an invariant divisor through a precomputed reciprocal
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): v = floor((2^64 - 1) / d) for d >= 1.  Then
+// q = floor(n * v / 2^64) is floor(n / d) or one less (v <= 2^64 / d, and
+// n * v / 2^64 > n / d - 1 for n < 2^64); the remainder test fixes it.
+__device__ __forceinline__ u64 div_rcp(u64 n, u64 d, u64 v)
+{
+    u64 q = __umul64hi(n, v);
+    u64 r = n - q * d;
+    if (r >= d) {
+        q++;
+        r -= d;
+    }
+    if (r >= d) q++;
+    return q;
+}
 PC_HD u64 pc_max(u64 a, u64 b) { return a > b ? a : b; }
 
 // ----------------------------------------------------------- lookup tables
@@ -110,6 +129,7 @@ struct MList {
     const u32* m;
     const u32* info;
     const u32* gpf;   // prime index of the greatest prime factor
+    const u64* rcp;   // floor((2^64 - 1) / m)
     u64 n;
     u64 limit;        // every squarefree m <= limit with lpf(m) > p_cmin is listed
     u32 cmin;

@@ -41,7 +41,8 @@ extern "C" int pc_create(pc_ctx** out, int device, const pc_params* p)
     if (!ctx) return PC_ENOMEM;
     ctx->device = device;
     if (p) ctx->params = *p;
-    if (ctx->params.c > 7 || (ctx->params.seg_bytes && (ctx->params.seg_bytes % 1024 || ctx->params.seg_bytes > 196608)) ||
+    const uint32_t sb = ctx->params.seg_bytes;
+    if (ctx->params.c > 7 || (sb && sb != 1024 && sb != 2048 && (sb % 4096 || sb > 65536)) ||
         ctx->params.ctas_per_sm > 4 ||
         (ctx->params.threads && (ctx->params.threads % 32 || ctx->params.threads < 128 || ctx->params.threads > 1024))) {
         delete ctx;
@@ -74,7 +75,8 @@ extern "C" void pc_destroy(pc_ctx* ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     Tables& T = ctx->T;
-    DevBuf* bufs[] = {&T.small_primes, &T.pi_words, &T.pi_pcnt, &T.primes, &T.ml_m, &T.ml_info, &T.ml_gpf,
+    DevBuf* bufs[] = {&T.small_primes, &T.pi_words, &T.pi_pcnt, &T.primes, &T.primes_rcp, &T.ml_m, &T.ml_info,
+                      &T.ml_gpf, &T.ml_rcp,
                       &T.rank_bits, &T.rank_cnt, &ctx->seg_b, &ctx->seg_off, &ctx->counts, &ctx->tallies,
                       &ctx->acc_seg, &ctx->partials, &ctx->result, &ctx->misc, &ctx->scan_tmp, &ctx->queue,
                       &ctx->easy_rng, &ctx->easy_chunk_off};

@@ -1,35 +1,55 @@
 // pc_hard.cu -- the hard special leaves: the main sieve of Section 3 on the GPU.
 //
-// The interval [0, z] (z = x/y) is cut into segments of 30*seg_bytes
-// integers.  Each CTA owns one segment at a time as a mod-30 bitset in shared
-// memory and walks the primes p_b in order, b = k0+1 .. B_s:
+// The interval [0, z] (z = x/y) is cut into segments; a segment is split
+// into sub-ranges of sub_bytes bytes (30*sub_bytes integers, mod-30 wheel),
+// one per warp of the CTA that owns the segment.  Each warp walks the primes
+// p_b in order, b = k0+1 .. B_s, over its own sub-range only:
 //
-//   1. leaves of b (b > c): the segment's bitset holds the integers of the
-//      segment coprime to p_1..p_{b-1}, so for a hard leaf (b, m) with
-//      u = x/(p_b m) in the segment, phi(u, b-1) = phi(L-1, b-1) + local(u),
-//      local(u) = set bits in [L, u].  The CTA adds -mu(m) * local(u) to its
-//      sum and -mu(m) to tally(s, b): the unknown phi(L-1, b-1) is recorded,
-//      not needed, exactly as the tallies of Section 3.
-//   2. cross off the multiples of p_b, then record count(s, b), the set bits
-//      left in the segment.
+//   1. leaves of b (b > c): its bitset holds the integers of the sub-range
+//      coprime to p_1..p_{b-1}, so for a hard leaf (b, m) with
+//      u = x/(p_b m) in the sub-range, phi(u, b-1) = phi(L_w - 1, b-1) +
+//      local(u), local(u) = set bits in [L_w, u].  The warp adds
+//      -mu(m) * local(u) to its sum and -mu(m) to its tally for b: the unknown
+//      phi(L_w - 1, b-1) is recorded, not needed, exactly as the tallies of
+//      Section 3.
+//   2. cross off the multiples of p_b in the sub-range, then record its count
+//      of set bits.
 //
-// Afterwards phi(L_s - 1, b-1) = sum_{s' < s} count(s', b-1) is an exclusive
-// scan over segments (the carries), and
-//   S2_hard = sum_s acc(s) + sum_{s,b} tally(s, b) * phi(L_s - 1, b - 1).
-// Segments are independent, so all SMs sieve at once and the sequential
-// "synchronization after each round" of Section 3 becomes one scan.
-//
-// local(u) uses per-1024-bit block counters, decremented when a bit is
-// cleared (or recounted after a small prime), a CTA scan of the block
-// counters when a step has leaves, and __popcll over the words of u's block.
+// Warps never wait for one another inside a batch of primes (only
+// __syncwarp); once per batch the CTA folds the warps' counts and tallies
+// into segment rows and settles the carries between its own sub-ranges.
+// Across segments, phi(L_s - 1, b - 1) = sum_{s' < s} count(s', b - 1) is an
+// exclusive scan (the carries), and
+//   S2_hard = sum (local sums) + sum_{s,b} tally(s, b) * phi(L_s - 1, b - 1).
+// All segments are sieved at once, so the "synchronization after each
+// round" of Section 3 becomes one scan.
 //
 // A hard leaf (b, m) has u < x / p_b^2, so a segment starting at L only
 // needs the primes p_b <= isqrt(x / L): B_s = pi(isqrt(x/L)).
+//
+// Load balance: hard leaves crowd near u = y (their density falls like
+// 1/u^2), so one segment can hold a large share of them.  A pre-pass counts
+// the leaves of every segment; heavy segments are handed to several CTAs
+// ("replicas"), each of which sieves the whole segment but resolves only its
+// share of every step's leaves (Section 3 mentions dynamic block scheduling;
+// here the schedule is a list of work items sorted by estimated cost).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "pc_internal.h"
 #include "pc_sieve.cuh"
 
-static constexpr u32 BATCH = 128;
-static constexpr u32 RECOUNT_P = 256;   // primes below this recount block counters
+static constexpr u32 BATCH = 64;
+static constexpr u32 EMAX = 64;        // multiples of one large prime in a segment (at most 48)
+static constexpr u32 RECOUNT_P = 128;   // below this a warp recounts its blocks after crossing off
+static constexpr u32 MAX_NW = 16;       // warps (sub-ranges) per segment
+static constexpr u32 MAX_SUB = 4096;    // bytes per sub-range: 32 blocks of 1024 bits
+
+struct HardItem {
+    u32 s;    // segment
+    u32 rR;   // replica r << 16 | replica count R
+};
 
 struct HardArgs {
     u64 x, y, z;
@@ -37,259 +57,383 @@ struct HardArgs {
     u64 a;
     bool trunc;
     u64 nseg;
-    u32 seg_bytes;
-    u64 span;
+    u32 seg_bytes, sub_bytes, nw, sub_shift;   // sub_bits = 1 << sub_shift
+    u64 span;     // integers per segment
+    u64 dspan;    // integers per sub-range
     PiTable pit;
     RankTable rk;
     MList ml;
     const u32* primes;
+    const u64* primes_rcp;
     const u32* segB;
     const u64* off;
     u32* counts;
     i32* tallies;
-    I128Pair* acc;
+    const HardItem* items;
+    u64 nitems;
+    I128Pair* acc;                 // one slot per CTA
     u32* queue;
-    unsigned long long* nleaves;   // [0] hard leaves, [1] multiples crossed off
+    unsigned long long* stat;      // [0] hard leaves, [1] multiples crossed off
 };
 
 struct StepInfo {
-    u64 xp;       // x / p_b
-    u64 kstart;   // first cofactor to cross off: max(p_b, ceil(L / p_b))
-    u64 i0, i1;   // leaf index range
+    u64 xp;        // x / p_b
+    u64 q;         // L / p_b
+    u64 mlo, mhi;  // leaf window m in (mlo, mhi]
+    u16 coff[8];   // floor(p * R8[j] / 30): byte offset of class j inside a wheel round
+    u8 cbit[8];    // bit of class j inside its byte
     u32 p;
-    u32 src;      // 0: m-list, 1: primes
+    u32 r0;        // L mod p_b
+    u32 flags;     // bit 0: leaves are primes, bit 1: step has leaves, bit 2: cross off by events
+    u32 ne;        // events (multiples of p_b in the segment), bit 2 only
+    u32 pself;     // segment bit of p_b itself, or ~0
+    u32 wmask;     // warps whose sub-range holds an event
 };
 
-// exclusive scan of blk[0..n) into pre[0..n], by the whole CTA
-template <int NT>
-__device__ __forceinline__ void cta_scan_blocks(const u32* blk, u32* pre, u32 n, u32* wsum)
+// leaf range of prime b in the segment [L, L + span): m in (mlo, mhi]
+__device__ __forceinline__ bool leaf_window(const HardArgs& A, u64 p, u64 xp, u64 L, u64& mlo, u64& mhi)
 {
-    const u32 per = (n + NT - 1) / NT;
-    const u32 t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    u32 b0 = t * per, b1 = b0 + per < n ? b0 + per : n;
-    u32 loc = 0;
-    for (u32 k = b0; k < b1; k++) loc += blk[k];
-    u32 incl = loc;
-    for (int o = 1; o < 32; o <<= 1) {
-        u32 v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        u32 w = lane < NT / 32 ? wsum[lane] : 0, wi = w;
-        for (int o = 1; o < 32; o <<= 1) {
-            u32 v = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += v;
-        }
-        if (lane < NT / 32) wsum[lane] = wi - w;
-    }
-    __syncthreads();
-    u32 run = wsum[wid] + incl - loc;
-    for (u32 k = b0; k < b1; k++) {
-        pre[k] = run;
-        run += blk[k];
-    }
-    if (t == NT - 1) pre[n] = run;
-    __syncthreads();
+    const u64 T = pc_min(p * p, A.y);     // hard: u >= min(p^2, y)
+    mhi = pc_min(A.y, xp / T);
+    if (L) mhi = pc_min(mhi, xp / L);     // u >= L
+    mlo = pc_max(A.y / p, xp / (L + A.span));   // u < L + span, and m > y / p
+    return mhi > mlo;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) hard_sieve_kernel(HardArgs A)
+// Crossing off needs no atomics: a warp owns its sub-range.  For a prime
+// below seg_bytes/4 the lanes take whole wheel rounds (30 p integers, p
+// bytes), even rounds first, then odd ones, so lanes of one pass touch words
+// at least 2p bytes apart.  Larger primes have at most 48 multiples in the
+// segment; the CTA lists them once per batch ("events") and each warp applies
+// those in its sub-range.  Multiples of one prime are >= p integers apart, so
+// lanes never share a word there either.
+__global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    StepInfo* step = (StepInfo*)smem_raw;
+    const u32 nw = A.nw, sub_bytes = A.sub_bytes, sub_words = sub_bytes >> 2, nbw = sub_bytes >> 7;
+    const u32 sub_bits = sub_bytes << 3;
+    StepInfo* st = (StepInfo*)smem_raw;
     u32* bits = (u32*)(smem_raw + BATCH * sizeof(StepInfo));
-    const u32 seg_words = A.seg_bytes >> 2;
-    const u32 nblk = A.seg_bytes >> 7;      // 1024-bit blocks
-    u32* blk = bits + seg_words;
-    u32* pre = blk + nblk;                  // nblk + 1 entries
-    const u64* bits64 = (const u64*)bits;
+    u32* blk = bits + (A.seg_bytes >> 2);          // nw * 32
+    u32* I = blk + nw * 32;                        // BATCH * (nw + 1)
+    u32* cw = I + BATCH * (nw + 1);                // BATCH * nw
+    i32* tw = (i32*)(cw + BATCH * nw);             // BATCH * nw
+    i32* basew = tw + BATCH * nw;                  // BATCH * nw
+    u32* ev = (u32*)(basew + BATCH * nw);          // BATCH * EMAX
+    u8* kmodw = (u8*)(ev + BATCH * EMAX);          // BATCH * nw
 
     __shared__ u32 patw[80];
-    __shared__ u32 wsum[32];
-    __shared__ u32 s_seg, s_total;
-    __shared__ u32 s_dec[2];
-    __shared__ int s_tally;
+    __shared__ u32 prev[MAX_NW];
+    __shared__ u32 s_item;
     __shared__ i128 red[32];
 
-    const u32 tid = threadIdx.x, lane = tid & 31;
+    const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5, NT = blockDim.x;
     make_pattern_words(patw, A.k0);
-    if (tid == 0) {
-        s_dec[0] = s_dec[1] = 0;
-        s_tally = 0;
-    }
+    u32* my = bits + w * sub_words;
+    const u64* my64 = (const u64*)my;
+    i64 acc = 0;
     unsigned long long nleaves = 0, nclears = 0;
 
     for (;;) {
-        if (tid == 0) {
-            s_seg = atomicAdd(A.queue, 1u);
-            s_total = 0;
-        }
         __syncthreads();
-        const u64 s = s_seg;
+        if (tid == 0) s_item = atomicAdd(A.queue, 1u);
         __syncthreads();
-        if (s >= A.nseg) break;
+        const u64 item = s_item;
+        if (item >= A.nitems) break;
+        const HardItem it = A.items[item];
+        const u64 s = it.s;
+        const u32 rep = it.rR >> 16, R = it.rR & 0xFFFFu;
         const u32 Bs = A.segB[s];
-        if (Bs <= A.k0) continue;
         const u64 L = s * A.span;
+        const u64 Lw = L + w * A.dspan;
 
-        fill_pattern(bits, seg_words, L, patw, A.k0);
+        fill_pattern(bits, A.seg_bytes >> 2, L, patw, A.k0);
         __syncthreads();
+        u32 cnt;
         {
-            u32 tot = 0;
-            for (u32 k = tid; k < nblk; k += NT) {
-                u32 c = 0;
-                for (u32 w = 0; w < 32; w++) c += __popc(bits[32 * k + w]);
-                blk[k] = c;
-                tot += c;
-            }
-            for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-            if (lane == 0) atomicAdd(&s_total, tot);
+            u32 c = 0;
+            if (lane < nbw)
+                for (u32 k = 0; k < 16; k++) c += __popcll(my64[lane * 16 + k]);
+            if (lane < nbw) blk[w * 32 + lane] = c;
+            cnt = __reduce_add_sync(0xffffffffu, c);
+            if (lane == 0) prev[w] = cnt;
         }
         __syncthreads();
-        if (tid == 0) A.counts[A.off[0] + s] = s_total;
+        if (tid == 0 && rep == 0) {
+            u32 t = 0;
+            for (u32 k = 0; k < nw; k++) t += prev[k];
+            A.counts[A.off[0] + s] = t;
+        }
 
-        i64 acc = 0;
         for (u32 bb = A.k0 + 1; bb <= Bs; bb += BATCH) {
             const u32 nb = Bs - bb + 1 < BATCH ? Bs - bb + 1 : BATCH;
             __syncthreads();
-            if (tid < nb) {
-                const u32 b = bb + tid;
+            // A: per-prime data of the batch
+            for (u32 t = tid; t < nb; t += NT) {
+                const u32 b = bb + t;
                 StepInfo si;
                 const u64 p = A.primes[b];
                 si.p = (u32)p;
                 si.xp = A.x / p;
-                u64 ks = L ? (L + p - 1) / p : 0;
-                si.kstart = ks < p ? p : ks;
-                si.i0 = si.i1 = 0;
-                si.src = 0;
-                if (b > A.kleaf && b <= A.a) {
-                    const u64 T = pc_min(p * p, A.y);
-                    u64 mhi = pc_min(A.y, si.xp / T);
-                    if (L) mhi = pc_min(mhi, si.xp / L);
-                    const u64 mlo = pc_max(A.y / p, si.xp / (L + A.span));
-                    if (mhi > mlo) {
-                        if (p * p > A.y) {
-                            u64 k0 = pc_max(pi_lookup(A.pit, mlo), b);
-                            u64 k1 = pc_min(pi_lookup(A.pit, mhi), A.a);
-                            if (k1 > k0) {
-                                si.i0 = k0 + 1;
-                                si.i1 = k1 + 1;
-                                si.src = 1;
-                            }
-                        } else {
-                            si.i0 = rank_lookup(A.rk, mlo);
-                            si.i1 = rank_lookup(A.rk, mhi);
-                        }
-                    }
-                }
-                step[tid] = si;
-            }
-            __syncthreads();
-
-            for (u32 t = 0; t < nb; t++) {
-                const u32 b = bb + t;
-                const u64 p = step[t].p;
-                if (b > A.kleaf) {
-                    const u64 i0 = step[t].i0, i1 = step[t].i1;
-                    if (i1 > i0) {
-                        cta_scan_blocks<NT>(blk, pre, nblk, wsum);
-                        const u64 xp = step[t].xp;
-                        const u32 src = step[t].src;
-                        int tl = 0;
-                        u32 nl = 0;
-                        for (u64 i = i0 + tid; i < i1; i += NT) {
-                            u64 m;
-                            bool neg;
-                            if (src) {
-                                m = A.primes[i];
-                                neg = true;
-                            } else {
-                                const u32 info = A.ml.info[i];
-                                if ((info >> 1) <= b) continue;
-                                if (A.trunc && A.ml.gpf[i] > A.a) continue;
-                                m = A.ml.m[i];
-                                neg = info & 1;
-                            }
-                            const u64 u = xp / m;
-                            const u32 e = seg_count_end(u, L);
-                            const u32 eb = e >> 10, ew = e >> 6;
-                            u32 cnt = pre[eb];
-                            for (u32 w = eb << 4; w < ew; w++) cnt += __popcll(bits64[w]);
-                            if (e & 63) cnt += __popcll(bits64[ew] & ((1ull << (e & 63)) - 1));
-                            acc += neg ? (i64)cnt : -(i64)cnt;
-                            tl += neg ? 1 : -1;
-                            nl++;
-                        }
-                        for (int o = 16; o; o >>= 1) {
-                            tl += __shfl_xor_sync(0xffffffffu, tl, o);
-                            nl += __shfl_xor_sync(0xffffffffu, nl, o);
-                        }
-                        if (lane == 0) {
-                            if (tl) atomicAdd(&s_tally, tl);
-                            nleaves += nl;
-                        }
-                        __syncthreads();
-                        if (tid == 0) {
-                            A.tallies[A.off[b - A.k0] + s] = s_tally;
-                            s_tally = 0;
-                        }
-                    } else if (tid == 0) {
-                        A.tallies[A.off[b - A.k0] + s] = 0;
-                    }
+                si.q = L / p;
+                si.r0 = (u32)(L - si.q * p);
+                si.flags = 0;
+                si.mlo = si.mhi = 0;
+                si.ne = 0;
+                si.wmask = 0;
+                si.pself = (p >= L && p < L + A.span) ? seg_pos(p, L) : ~0u;
+                if (b > A.kleaf && b <= A.a && leaf_window(A, p, si.xp, L, si.mlo, si.mhi))
+                    si.flags = 2u | (p * p > A.y ? 1u : 0u);
+                for (int j = 0; j < 8; j++) {
+                    si.coff[j] = 0;
+                    si.cbit[j] = 0;
                 }
                 if (b < Bs) {
-                    const u64 ks = step[t].kstart;
-                    u32 dec = 0;
-                    if (p < RECOUNT_P) {
-                        auto none = [](u32) {};
-                        nclears += cross_off_coop(bits, A.seg_bytes, L, (u32)p, ks, tid, NT, none);
-                        if (tid == 0 && p >= L && p < L + A.span) {
-                            u32 pos = seg_pos(p, L);
-                            atomicAnd(&bits[pos >> 5], ~(1u << (pos & 31)));
+                    if (p * 4 >= A.seg_bytes) {
+                        si.flags |= 4u;
+                        u64 k = si.q + (si.r0 != 0);
+                        if (k < p) k = p;
+                        k = coprime30_at_or_after(k);
+                        u32 r = (u32)(k % 30);
+                        u64 n = k * p;
+                        const u64 end = L + A.span;
+                        u32 ne = 0, wm = 0;
+                        while (n < end && ne < EMAX) {
+                            const u32 pos = seg_pos(n, L);
+                            ev[t * EMAX + ne++] = pos;
+                            wm |= 1u << (pos >> A.sub_shift);
+                            const u32 d = c_NEXT30[r];
+                            r += d;
+                            if (r >= 30) r -= 30;
+                            n += p * d;
                         }
-                        __syncthreads();
-                        for (u32 k = tid; k < nblk; k += NT) {
-                            u32 c = 0;
-                            for (u32 w = 0; w < 32; w++) c += __popc(bits[32 * k + w]);
-                            dec += blk[k] - c;
-                            blk[k] = c;
-                        }
+                        si.ne = ne;
+                        si.wmask = wm;
                     } else {
-                        auto newly = [&](u32 pos) {
-                            atomicSub(&blk[pos >> 10], 1u);
-                            dec++;
-                        };
-                        const u64 rounds = A.seg_bytes / p + 2;
-                        u32 nt = rounds * 8 >= NT ? NT : (u32)((rounds * 8 + 31) & ~31ull);
-                        if (tid < nt) nclears += cross_off_coop(bits, A.seg_bytes, L, (u32)p, ks, tid, nt, newly);
-                        if (tid == 0 && p >= L && p < L + A.span) {
-                            u32 pos = seg_pos(p, L);
-                            u32 msk = 1u << (pos & 31);
-                            if (atomicAnd(&bits[pos >> 5], ~msk) & msk) newly(pos);
+                        for (int j = 0; j < 8; j++) {
+                            const u32 pr = (u32)p * c_R8[j];
+                            si.coff[j] = (u16)(pr / 30);
+                            si.cbit[j] = c_IDX30[pr % 30];
                         }
-                    }
-                    for (int o = 16; o; o >>= 1) dec += __shfl_xor_sync(0xffffffffu, dec, o);
-                    if (lane == 0 && dec) atomicAdd(&s_dec[b & 1], dec);
-                    __syncthreads();
-                    if (tid == 0) {
-                        s_total -= s_dec[b & 1];
-                        s_dec[b & 1] = 0;
-                        A.counts[A.off[b - A.k0] + s] = s_total;
                     }
                 }
+                st[t] = si;
             }
+            __syncthreads();
+            // B: leaf index boundaries of every sub-range, and first wheel rounds
+            for (u32 idx = tid; idx < nb * (nw + 1); idx += NT) {
+                const u32 t = idx / (nw + 1), k = idx - t * (nw + 1);
+                const StepInfo& si = st[t];
+                u32 v32 = 0;
+                if (si.flags & 2u) {
+                    u64 v;
+                    if (k == 0) v = si.mhi;
+                    else if (k == nw) v = si.mlo;
+                    else v = pc_max(pc_min(si.xp / (L + k * A.dspan), si.mhi), si.mlo);
+                    if (si.flags & 1u) {
+                        const u64 b = bb + t;
+                        v32 = (u32)(pc_min(pc_max(pi_lookup(A.pit, v), b), A.a) + 1);
+                    } else {
+                        v32 = (u32)rank_lookup(A.rk, v);
+                    }
+                }
+                I[idx] = v32;
+            }
+            for (u32 idx = tid; idx < nb * nw; idx += NT) {
+                const u32 t = idx / nw, k = idx - t * nw;
+                const StepInfo& si = st[t];
+                if (si.flags & 4u || bb + t >= Bs) continue;
+                const u64 p = si.p;
+                u64 klo = si.q + (si.r0 + (u32)(k * A.dspan) + si.p - 1) / si.p;   // ceil(L_k / p)
+                if (klo < p) klo = p;
+                const u64 qa = klo / 30;
+                const i64 base = (i64)(p * qa) - (i64)(L / 30 + (u64)k * sub_bytes);
+                basew[idx] = base > (i64)sub_bytes ? (i32)sub_bytes : (i32)base;
+                kmodw[idx] = (u8)(klo - 30 * qa);
+            }
+            __syncthreads();
+            // C: every warp runs the batch over its own sub-range
+            for (u32 t = 0; t < nb; t++) {
+                const u32 b = bb + t;
+                const u32 fl = st[t].flags;
+                if (b > A.kleaf) {
+                    int tl = 0;
+                    if (fl & 2u) {
+                        u32 j0 = I[t * (nw + 1) + w + 1], j1 = I[t * (nw + 1) + w];
+                        if (R > 1 && j1 > j0) {
+                            const u64 n = j1 - j0;
+                            const u32 a0 = j0 + (u32)(n * rep / R), a1 = j0 + (u32)(n * (rep + 1) / R);
+                            j0 = a0;
+                            j1 = a1;
+                        }
+                        if (j1 > j0) {
+                            u32 pre = lane < nbw ? blk[w * 32 + lane] : 0;
+                            {
+                                u32 incl = pre;
+                                for (int o = 1; o < 32; o <<= 1) {
+                                    u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+                                    if (lane >= o) incl += v;
+                                }
+                                pre = incl - pre;
+                            }
+                            const u64 xp = st[t].xp;
+                            for (u32 base = j0; base < j1; base += 32) {
+                                const u32 i = base + lane;
+                                bool ok = i < j1;
+                                u64 m = 1, v = ~0ull;
+                                bool neg = true;
+                                if (ok) {
+                                    if (fl & 1u) {
+                                        m = A.primes[i];
+                                        v = A.primes_rcp[i];
+                                    } else {
+                                        const u32 info = A.ml.info[i];
+                                        ok = (info >> 1) > b && !(A.trunc && A.ml.gpf[i] > A.a);
+                                        m = A.ml.m[i];
+                                        v = A.ml.rcp[i];
+                                        neg = info & 1u;
+                                    }
+                                }
+                                const u64 u = ok ? div_rcp(xp, m, v) : Lw;
+                                const u32 e = seg_count_end(u, Lw);
+                                u32 bi = e >> 10;
+                                if (bi >= nbw) bi = nbw - 1;
+                                const u32 pb = __shfl_sync(0xffffffffu, pre, bi);
+                                if (ok) {
+                                    u32 c = pb;
+                                    const u32 ew = e >> 6;
+                                    for (u32 ww = bi << 4; ww < ew; ww++) c += __popcll(my64[ww]);
+                                    if (e & 63) c += __popcll(my64[ew] & ((1ull << (e & 63)) - 1));
+                                    acc += neg ? (i64)c : -(i64)c;
+                                    tl += neg ? 1 : -1;
+                                    nleaves++;
+                                }
+                            }
+                            tl = __reduce_add_sync(0xffffffffu, (u32)tl);
+                        }
+                    }
+                    if (lane == 0) tw[t * nw + w] = tl;
+                }
+                if (b < Bs) {
+                    const u32 p = st[t].p;
+                    const bool recount = p < RECOUNT_P;
+                    u32 dec = 0;
+                    auto clear_bit = [&](u32 pos) {   // pos: bit inside this warp's sub-range
+                        const u32 mask = 1u << (pos & 31);
+                        const u32 old = my[pos >> 5];
+                        if (old & mask) {
+                            my[pos >> 5] = old & ~mask;
+                            dec++;
+                            if (!recount) atomicSub(&blk[w * 32 + (pos >> 10)], 1u);
+                        }
+                    };
+                    if (fl & 4u) {
+                        // large prime: its few multiples, listed by the CTA
+                        if ((st[t].wmask >> w) & 1u) {
+                            const u32 ne = st[t].ne;
+                            for (u32 e = lane; e < ne; e += 32) {
+                                const u32 pos = ev[t * EMAX + e];
+                                if ((pos >> A.sub_shift) == w) {
+                                    clear_bit(pos & (sub_bits - 1));
+                                    nclears++;
+                                }
+                            }
+                        }
+                    } else {
+                        const i32 base = basew[t * nw + w];
+                        if (base < (i32)sub_bytes) {
+                            const u32 kmod = kmodw[t * nw + w];
+                            const uint4 cv = *(const uint4*)st[t].coff;
+                            const uint2 bv = *(const uint2*)st[t].cbit;
+                            const u32 cw4[4] = {cv.x, cv.y, cv.z, cv.w};
+                            if (p >= 128) {
+                                // lane = (class j, round offset o): four rounds per pass.
+                                // Two crossings of one prime p >= 128 by different lanes
+                                // are >= 4 bytes apart, so no two lanes share a word.
+                                const u32 j = lane & 7, o = lane >> 3;
+                                const u32 half = j >> 1;
+                                const u32 cword = half == 0 ? cv.x : half == 1 ? cv.y : half == 2 ? cv.z : cv.w;
+                                const u32 cj = (cword >> (16 * (j & 1))) & 0xFFFFu;
+                                const u32 bj = ((j < 4 ? bv.x : bv.y) >> (8 * (j & 3))) & 0xFFu;
+                                for (u32 r = o;; r += 4) {
+                                    const i64 by = (i64)base + (i64)p * r + cj;
+                                    if (by >= (i64)sub_bytes) break;
+                                    if (by < 0 || (r == 0 && c_R8[j] < kmod)) continue;
+                                    clear_bit(((u32)by << 3) + bj);
+                                    nclears++;
+                                }
+                            } else {
+                                // lane = whole wheel rounds, even rounds first, then odd ones
+                                for (u32 ph = 0; ph < 2; ph++) {
+                                    for (u32 r = 2 * lane + ph;; r += 64) {
+                                        const i64 b0 = (i64)base + (i64)p * r;
+                                        if (b0 >= (i64)sub_bytes) break;
+#pragma unroll
+                                        for (int jj = 0; jj < 8; jj++) {
+                                            if (r == 0 && c_R8[jj] < kmod) continue;
+                                            const i64 by = b0 + (i64)((cw4[jj >> 1] >> (16 * (jj & 1))) & 0xFFFFu);
+                                            if (by >= (i64)sub_bytes) break;
+                                            if (by < 0) continue;
+                                            const u32 bit = ((jj < 4 ? bv.x : bv.y) >> (8 * (jj & 3))) & 0xFFu;
+                                            clear_bit(((u32)by << 3) + bit);
+                                            nclears++;
+                                        }
+                                    }
+                                    __syncwarp();
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    const u32 ps = st[t].pself;
+                    if (lane == 0 && ps != ~0u && (ps >> A.sub_shift) == w) clear_bit(ps & (sub_bits - 1));
+                    if (recount) {
+                        __syncwarp();
+                        u32 c = 0;
+                        if (lane < nbw)
+                            for (u32 k = 0; k < 16; k++) c += __popcll(my64[lane * 16 + k]);
+                        if (lane < nbw) blk[w * 32 + lane] = c;
+                        cnt = __reduce_add_sync(0xffffffffu, c);
+                    } else {
+                        cnt -= __reduce_add_sync(0xffffffffu, dec);
+                    }
+                }
+                if (lane == 0) cw[t * nw + w] = cnt;
+                __syncwarp();
+            }
+            __syncthreads();
+            // D: segment rows, and the carries between the CTA's sub-ranges
+            for (u32 t = tid; t < nb; t += NT) {
+                const u32 b = bb + t;
+                u32 C = 0;
+                for (u32 k = 0; k < nw; k++) C += cw[t * nw + k];
+                if (rep == 0 && b < Bs) A.counts[A.off[b - A.k0] + s] = C;
+                if (b > A.kleaf) {
+                    const u32* cp = t ? cw + (t - 1) * nw : prev;
+                    i32 T = 0;
+                    i64 intra = 0, run = 0;
+                    for (u32 k = 0; k < nw; k++) {
+                        const i32 tk = tw[t * nw + k];
+                        T += tk;
+                        intra += (i64)tk * run;
+                        run += cp[k];
+                    }
+                    if (T) atomicAdd(&A.tallies[A.off[b - A.k0] + s], T);
+                    acc += intra;
+                }
+            }
+            __syncthreads();
+            if (tid < nw) prev[tid] = cw[(nb - 1) * nw + tid];
         }
-        i128 tot = block_sum_i128((i128)acc, red);
-        if (tid == 0) store_i128(A.acc + s, tot);
     }
+    i128 tot = block_sum_i128((i128)acc, red);
+    if (tid == 0) store_i128(A.acc + blockIdx.x, tot);
     for (int o = 16; o; o >>= 1) {
         nleaves += __shfl_xor_sync(0xffffffffu, nleaves, o);
         nclears += __shfl_xor_sync(0xffffffffu, nclears, o);
     }
-    if (lane == 0 && nleaves) atomicAdd(A.nleaves, nleaves);
-    if (lane == 0 && nclears) atomicAdd(A.nleaves + 1, nclears);
+    if (lane == 0 && nleaves) atomicAdd(A.stat, nleaves);
+    if (lane == 0 && nclears) atomicAdd(A.stat + 1, nclears);
 }
 
 // ---------------------------------------------------------- schedule
@@ -319,6 +463,36 @@ __global__ void row_len_kernel(const u32* segB, u64 nseg, u32 k0, u32 bmax, u32*
         if (segB[mid] >= b) lo = mid + 1; else hi = mid;
     }
     len[t] = (u32)lo;
+}
+
+// Upper bound of the hard leaves of every segment (the lpf filter of the
+// m-list is not applied): one thread per (b, s) row entry.
+__global__ void hard_estimate_kernel(HardArgs A, u64 total, u32 nrows, unsigned long long* est)
+{
+    for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (u64)gridDim.x * blockDim.x) {
+        u32 lo = 0, hi = nrows;   // largest row with off[row] <= e
+        while (hi - lo > 1) {
+            u32 mid = (lo + hi) >> 1;
+            if (A.off[mid] <= e) lo = mid; else hi = mid;
+        }
+        const u64 b = A.k0 + lo;
+        if (b <= A.kleaf || b > A.a) continue;
+        const u64 s = e - A.off[lo];
+        const u64 L = s * A.span;
+        const u64 p = A.primes[b];
+        const u64 xp = A.x / p;
+        u64 mlo, mhi;
+        if (!leaf_window(A, p, xp, L, mlo, mhi)) continue;
+        u64 n;
+        if (p * p > A.y) {
+            const u64 k0 = pc_min(pc_max(pi_lookup(A.pit, mlo), b), A.a);
+            const u64 k1 = pc_min(pc_max(pi_lookup(A.pit, mhi), b), A.a);
+            n = k1 - k0;
+        } else {
+            n = rank_lookup(A.rk, mhi) - rank_lookup(A.rk, mlo);
+        }
+        if (n) atomicAdd(est + s, (unsigned long long)n);
+    }
 }
 
 // S2_hard carries: for each leaf prime b, the exclusive scan over segments
@@ -375,24 +549,53 @@ __global__ void __launch_bounds__(NT) hard_combine_kernel(HardArgs A, I128Pair* 
 u32 pc_seg_bytes(pc_ctx* ctx)
 {
     u32 sb = ctx->params.seg_bytes;
-    if (sb == 0) sb = 65536;
-    sb = (sb + 1023) & ~1023u;
+    if (sb == 0) sb = MAX_NW * MAX_SUB;
     if (sb < 1024) sb = 1024;
-    if (sb > 196608) sb = 196608;
+    if (sb > MAX_NW * MAX_SUB) sb = MAX_NW * MAX_SUB;
+    if (sb > MAX_SUB) sb = sb / MAX_SUB * MAX_SUB;
+    else if (sb > 2048) sb = 4096 > sb ? 2048 : 4096;   // sub-ranges are powers of two
+    else sb = sb / 1024 * 1024;
     return sb;
 }
 
-template <int NT>
-static int launch_hard(pc_ctx* ctx, const HardArgs& A, int ctas, size_t smem)
+// Work items: segments, heavy ones split into replicas; sorted by estimated
+// cost, heaviest first.  Costs in units of one leaf: one (segment, prime)
+// step of all warps costs about STEP_COST leaves, one crossing-off about
+// CLEAR_COST.  A segment's crossings are estimated by Mertens' theorem,
+// span * 8/30 * sum_{13 <= p <= P} 1/p ~ span * 8/30 * (ln ln P - 1.0056),
+// P = isqrt(x / L), the largest prime the segment sieves with.
+static void plan_items(const std::vector<u32>& segB, const std::vector<unsigned long long>& est, u32 k0, int ctas,
+                       u64 x, u64 z, u64 span, std::vector<HardItem>& items)
 {
-    cudaError_t e = cudaFuncSetAttribute(hard_sieve_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) {
-        pc_set_error(ctx, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(e));
-        return PC_ECUDA;
+    const double STEP_COST = 48.0, CLEAR_COST = 0.08;
+    const size_t nseg = segB.size();
+    std::vector<double> base(nseg);
+    double total = 0;
+    for (size_t s = 0; s < nseg; s++) {
+        const double steps = segB[s] > k0 ? (double)(segB[s] - k0) : 0.0;
+        const u64 P = s ? pc_min(pc_isqrt(x / (s * span)), pc_isqrt(z)) : pc_isqrt(z);
+        const double ll = P > 16 ? std::log(std::log((double)P)) - 1.0056 : 0.0;
+        base[s] = STEP_COST * steps + CLEAR_COST * (double)span * (8.0 / 30.0) * (ll > 0 ? ll : 0.0);
+        total += base[s] + (double)est[s];
     }
-    hard_sieve_kernel<NT><<<ctas, NT, smem, ctx->stream>>>(A);
-    PC_LAUNCHED(ctx);
-    return PC_OK;
+    const double target = std::max(total / (ctas * 4.0), 1.0);
+    std::vector<std::pair<double, HardItem>> v;
+    v.reserve(nseg + 64);
+    for (size_t s = 0; s < nseg; s++) {
+        if (segB[s] <= k0) continue;
+        u32 R = 1;
+        if (base[s] + (double)est[s] > target && (double)est[s] > base[s]) {
+            // split the leaves while a replica's leaf share still outweighs its sieve
+            const double room = std::max(target - base[s], base[s]);
+            R = (u32)std::min(1024.0, std::ceil((double)est[s] / std::max(room, 1.0)));
+            if (R < 1) R = 1;
+        }
+        for (u32 r = 0; r < R; r++)
+            v.push_back({base[s] + (double)est[s] / R, HardItem{(u32)s, (r << 16) | R}});
+    }
+    std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    items.resize(v.size());
+    for (size_t i = 0; i < v.size(); i++) items[i] = v[i].second;
 }
 
 int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
@@ -406,64 +609,95 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     A.kleaf = P.c > A.k0 ? P.c : A.k0;
     A.a = P.a;
     A.trunc = P.trunc;
-    u64 bmax = P.B < P.a ? P.B : P.a;
+    const u64 bmax = P.B < P.a ? P.B : P.a;
     if (bmax <= A.kleaf) return PC_OK;   // no hard leaf needs the sieve
     A.bmax = (u32)bmax;
     A.seg_bytes = pc_seg_bytes(ctx);
+    A.sub_bytes = A.seg_bytes < MAX_SUB ? A.seg_bytes : MAX_SUB;
+    A.nw = A.seg_bytes / A.sub_bytes;
+    A.sub_shift = 3;
+    while ((1u << A.sub_shift) < A.sub_bytes * 8) A.sub_shift++;
     A.span = 30ull * A.seg_bytes;
+    A.dspan = 30ull * A.sub_bytes;
     A.nseg = P.z / A.span + 1;
     A.pit = ctx->T.pi();
     A.rk = ctx->T.rank();
     A.ml = ctx->T.mlist();
     A.primes = ctx->T.primes.as<u32>();
+    A.primes_rcp = ctx->T.primes_rcp.as<u64>();
 
     const u64 nrows = bmax - A.k0 + 1;
     PC_TRY(buf_reserve(ctx, ctx->seg_b, A.nseg * sizeof(u32) + (nrows + 1) * sizeof(u32)));
-    PC_TRY(buf_reserve(ctx, ctx->seg_off, (nrows + 1) * sizeof(u64)));
+    PC_TRY(buf_reserve(ctx, ctx->seg_off, (nrows + 1) * sizeof(u64) + A.nseg * sizeof(u64)));
     u32* segB = ctx->seg_b.as<u32>();
     u32* rowlen = segB + A.nseg;
     u64* off = ctx->seg_off.as<u64>();
+    unsigned long long* est = (unsigned long long*)(off + nrows + 1);
     seg_b_kernel<<<(unsigned)((A.nseg + 255) / 256), 256, 0, ctx->stream>>>(P.x, A.nseg, A.span, A.bmax, A.pit, segB);
     PC_LAUNCHED(ctx);
     row_len_kernel<<<(unsigned)((nrows + 255) / 256), 256, 0, ctx->stream>>>(segB, A.nseg, A.k0, A.bmax, rowlen);
     PC_LAUNCHED(ctx);
     ctx->stats.kernel_launches += 2;
     PC_TRY(scan_exclusive_u32_to_u64(ctx, rowlen, off, nrows));
-    u64 total = 0;
-    PC_TRY(copy_to_host(ctx, &total, off + nrows, sizeof(u64)));
-    PC_TRY(buf_reserve(ctx, ctx->counts, total * sizeof(u32)));
-    PC_TRY(buf_reserve(ctx, ctx->tallies, total * sizeof(i32)));
-    PC_TRY(buf_reserve(ctx, ctx->acc_seg, A.nseg * sizeof(I128Pair)));
-    PC_TRY(buf_reserve(ctx, ctx->queue, 64));
-    PC_CUDA(ctx, cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream));
-    PC_CUDA(ctx, cudaMemsetAsync(ctx->acc_seg.p, 0, A.nseg * sizeof(I128Pair), ctx->stream));
     A.segB = segB;
     A.off = off;
-    A.counts = ctx->counts.as<u32>();
-    A.tallies = ctx->tallies.as<i32>();
-    A.acc = ctx->acc_seg.as<I128Pair>();
-    A.queue = ctx->queue.as<u32>();
-    A.nleaves = (unsigned long long*)(ctx->queue.as<u32>() + 2);
+    u64 total = 0;
+    PC_TRY(copy_to_host(ctx, &total, off + nrows, sizeof(u64)));
 
-    int nt = ctx->params.threads ? (int)ctx->params.threads : 512;
+    // per-segment leaf estimate, then the work items
+    PC_CUDA(ctx, cudaMemsetAsync(est, 0, A.nseg * sizeof(u64), ctx->stream));
+    hard_estimate_kernel<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, total, (u32)nrows, est);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    std::vector<u32> hsegB(A.nseg);
+    std::vector<unsigned long long> hest(A.nseg);
+    PC_CUDA(ctx, cudaMemcpyAsync(hsegB.data(), segB, A.nseg * sizeof(u32), cudaMemcpyDeviceToHost, ctx->stream));
+    PC_CUDA(ctx, cudaMemcpyAsync(hest.data(), est, A.nseg * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    PC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+
+    const u32 nbw = A.sub_bytes >> 7;
+    (void)nbw;
+    const size_t smem = BATCH * sizeof(StepInfo) + A.seg_bytes + (size_t)A.nw * 32 * 4 +
+                        (size_t)BATCH * (A.nw + 1) * 4 + 3 * (size_t)BATCH * A.nw * 4 + (size_t)BATCH * EMAX * 4 +
+                        (size_t)BATCH * A.nw;
     int per_sm = ctx->params.ctas_per_sm ? (int)ctx->params.ctas_per_sm : 0;
-    const u32 nblk = A.seg_bytes >> 7;
-    size_t smem = BATCH * sizeof(StepInfo) + A.seg_bytes + (2 * (size_t)nblk + 2) * sizeof(u32);
     if (per_sm == 0) {
-        per_sm = (int)(ctx->smem_optin / (smem + 4096));
+        per_sm = (int)(ctx->smem_optin / (smem + 2048));
         if (per_sm < 1) per_sm = 1;
         if (per_sm > 4) per_sm = 4;
+        if (per_sm > 2 && A.nw >= 8) per_sm = 2;   // launch bounds: 2 CTAs of 512 threads
     }
     int ctas = ctx->sm_count * per_sm;
-    if ((u64)ctas > A.nseg) ctas = (int)A.nseg;
 
+    std::vector<HardItem> items;
+    plan_items(hsegB, hest, A.k0, ctas, P.x, P.z, A.span, items);
+    A.nitems = items.size();
+    PC_TRY(buf_reserve(ctx, ctx->counts, total * sizeof(u32)));
+    PC_TRY(buf_reserve(ctx, ctx->tallies, total * sizeof(i32)));
+    PC_TRY(buf_reserve(ctx, ctx->acc_seg, (size_t)ctas * sizeof(I128Pair) + items.size() * sizeof(HardItem) + 64));
+    PC_TRY(buf_reserve(ctx, ctx->queue, 64));
+    HardItem* ditems = (HardItem*)(ctx->acc_seg.as<I128Pair>() + ctas);
+    if (!items.empty())
+        PC_CUDA(ctx, cudaMemcpyAsync(ditems, items.data(), items.size() * sizeof(HardItem), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    PC_CUDA(ctx, cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream));
+    PC_CUDA(ctx, cudaMemsetAsync(ctx->tallies.p, 0, total * sizeof(i32), ctx->stream));
+    A.counts = ctx->counts.as<u32>();
+    A.tallies = ctx->tallies.as<i32>();
+    A.items = ditems;
+    A.acc = ctx->acc_seg.as<I128Pair>();
+    A.queue = ctx->queue.as<u32>();
+    A.stat = (unsigned long long*)(ctx->queue.as<u32>() + 2);
+
+    cudaError_t e = cudaFuncSetAttribute(hard_sieve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        pc_set_error(ctx, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(e));
+        return PC_ECUDA;
+    }
     cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
     PC_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-    int rc;
-    if (nt <= 256) rc = launch_hard<256>(ctx, A, ctas, smem);
-    else if (nt <= 512) rc = launch_hard<512>(ctx, A, ctas, smem);
-    else rc = launch_hard<1024>(ctx, A, ctas, smem);
-    if (rc) return rc;
+    hard_sieve_kernel<<<ctas, 32 * A.nw, smem, ctx->stream>>>(A);
+    PC_LAUNCHED(ctx);
     PC_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
     ctx->stats.kernel_launches++;
 
@@ -473,10 +707,10 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     PC_LAUNCHED(ctx);
     ctx->stats.kernel_launches++;
     PC_TRY(reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out));
-    PC_TRY(reduce_i128(ctx, A.acc, A.nseg, out));
+    PC_TRY(reduce_i128(ctx, A.acc, ctas, out));
 
     u64 nl[2] = {0, 0};
-    PC_TRY(copy_to_host(ctx, nl, A.nleaves, 2 * sizeof(u64)));
+    PC_TRY(copy_to_host(ctx, nl, A.stat, 2 * sizeof(u64)));
     float ms = 0;
     PC_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
     ctx->stats.ms_hard_sieve = ms;

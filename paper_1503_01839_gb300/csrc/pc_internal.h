@@ -56,18 +56,22 @@ struct Tables {
     u64 prime_limit = 0;
     u64 nprimes = 0;
     DevBuf primes;
+    DevBuf primes_rcp;   // floor((2^64 - 1) / p_k), same indexing as primes
     // squarefree m-list over [2, ml_limit] with lpf > p_cmin
     u64 ml_limit = 0;
     u32 ml_cmin = 99;
     u64 ml_n = 0;
-    DevBuf ml_m, ml_info, ml_gpf, rank_bits, rank_cnt;
+    DevBuf ml_m, ml_info, ml_gpf, ml_rcp, rank_bits, rank_cnt;
     // phi(., c) residue tables for the primorial of c (c = 0..7)
     DevBuf phiT[8];
     bool phiT_ok[8] = {false, false, false, false, false, false, false, false};
 
     PiTable pi() const { return PiTable{pi_words.as<u64>(), pi_pcnt.as<u32>(), pi_limit}; }
     RankTable rank() const { return RankTable{rank_bits.as<u64>(), rank_cnt.as<u32>(), ml_limit}; }
-    MList mlist() const { return MList{ml_m.as<u32>(), ml_info.as<u32>(), ml_gpf.as<u32>(), ml_n, ml_limit, ml_cmin}; }
+    MList mlist() const
+    {
+        return MList{ml_m.as<u32>(), ml_info.as<u32>(), ml_gpf.as<u32>(), ml_rcp.as<u64>(), ml_n, ml_limit, ml_cmin};
+    }
 };
 
 // ---------------------------------------------------------------- context

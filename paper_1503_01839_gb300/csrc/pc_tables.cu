@@ -243,6 +243,13 @@ __global__ void mlist_scatter_kernel(const u64* info_tmp, const u64* rbits, cons
     mgpf[idx] = (u32)(packed >> 32);
 }
 
+// reciprocals v = floor((2^64 - 1) / d) of a u32 array (d >= 1; d = 0 gives 0)
+__global__ void reciprocal_kernel(const u32* d, u64 n, u64* v)
+{
+    u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = d[i] ? ~0ull / d[i] : 0;
+}
+
 // ------------------------------------------------------------ phi tables
 __global__ void coprime_flags_kernel(u32 Q, u32 c, const u32* sp, u32* flags)
 {
@@ -318,7 +325,11 @@ static int build_primes(pc_ctx* ctx, u64 prime_limit)
     extract_primes_kernel<<<(unsigned)((wlim + 255) / 256), 256, 0, ctx->stream>>>(
         T.pi_words.as<u64>(), T.pi_pcnt.as<u32>(), wlim, T.primes.as<u32>(), n_out);
     PC_LAUNCHED(ctx);
-    ctx->stats.kernel_launches++;
+    PC_TRY(buf_reserve(ctx, T.primes_rcp, (n_out + 2) * sizeof(u64)));
+    reciprocal_kernel<<<(unsigned)((n_out + 1 + 255) / 256), 256, 0, ctx->stream>>>(T.primes.as<u32>(), n_out + 1,
+                                                                                   T.primes_rcp.as<u64>());
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches += 2;
     T.nprimes = np;
     T.prime_limit = prime_limit;
     return PC_OK;
@@ -358,11 +369,17 @@ static int build_mlist(pc_ctx* ctx, u64 Y, u32 cmin)
     if (rc == PC_OK) rc = buf_reserve(ctx, T.ml_m, ((u64)total + 1) * sizeof(u32));
     if (rc == PC_OK) rc = buf_reserve(ctx, T.ml_info, ((u64)total + 1) * sizeof(u32));
     if (rc == PC_OK) rc = buf_reserve(ctx, T.ml_gpf, ((u64)total + 1) * sizeof(u32));
+    if (rc == PC_OK) rc = buf_reserve(ctx, T.ml_rcp, ((u64)total + 1) * sizeof(u64));
     if (rc == PC_OK) {
         mlist_scatter_kernel<<<(unsigned)((Y + 256) / 256), 256, 0, ctx->stream>>>(
             info_tmp.as<u64>(), T.rank_bits.as<u64>(), T.rank_cnt.as<u32>(), Y, T.ml_m.as<u32>(),
             T.ml_info.as<u32>(), T.ml_gpf.as<u32>());
         e = cudaGetLastError();
+        if (e == cudaSuccess && total) {
+            reciprocal_kernel<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(T.ml_m.as<u32>(), total,
+                                                                                      T.ml_rcp.as<u64>());
+            e = cudaGetLastError();
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) {
             pc_set_error(ctx, "m-list build: %s", cudaGetErrorString(e));

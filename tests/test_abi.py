@@ -58,5 +58,5 @@ def test_create_without_gpu_fails_cleanly(libpath):
 
 def test_bad_params_rejected_before_device_work(libpath):
     with pytest.raises(pc.PicountError) as e:
-        pc.Context(0, seg_bytes=1000)
+        pc.Context(0, seg_bytes=5120)
     assert e.value.code == -1
