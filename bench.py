@@ -192,6 +192,29 @@ def run_reference(args):
     return 0
 
 
+def run_pi_mode(args):
+    """Whole pi(x) evaluations through the C ABI (all phases), one per step."""
+    import torch
+    import paper_1503_01839_gb300 as pc
+    from paper_1503_01839_gb300 import build as pcbuild
+    pcbuild.build()
+    ctx = pc.Context(0, seg_bytes=args.seg_bytes)
+    for _ in range(max(1, args.warmup)):
+        ref = ctx.pi_count(X, ALPHA)
+    ts = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        assert ctx.pi_count(X, ALPHA) == ref
+        ts.append(time.perf_counter() - t0)
+    st = ctx.stats()
+    print(json.dumps({"mode": "pi", "x": X, "alpha": ALPHA, "pi": ref, "ms_per_step": 1000 * statistics.mean(ts),
+                      "phases_ms": {k: round(st[k], 3) for k in ("ms_tables", "ms_s1", "ms_trivial", "ms_easy",
+                                                                  "ms_hard", "ms_p2")}}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -203,9 +226,13 @@ def main():
     ap.add_argument("--no-pi", action="store_true", help="skip the pi(1e16)/pi(1e18) wall-time lines")
     ap.add_argument("--x", type=float, default=1e18, help="profiling only: a smaller x than the benchmark's")
     ap.add_argument("--alpha", type=int, default=20)
+    ap.add_argument("--mode", default="s2_hard", choices=["s2_hard", "pi"],
+                    help="pi: time whole pi(x) evaluations instead (profiling aid)")
     args = ap.parse_args()
     global X, ALPHA
     X, ALPHA = int(args.x), args.alpha
+    if args.mode == "pi":
+        return run_pi_mode(args)
     if args.impl == "reference":
         return run_reference(args)
 

@@ -22,20 +22,22 @@ typedef unsigned __int128 u128;
 
 #define PC_HD __host__ __device__ __forceinline__
 
-// ------------------------------------------------------------- wheel tables
-static __constant__ unsigned char c_R8[8] = {1, 7, 11, 13, 17, 19, 23, 29};
-// index of residue r in R8, 255 if r shares a factor with 30
-static __constant__ unsigned char c_IDX30[30] = {
-    255, 0, 255, 255, 255, 255, 255, 1, 255, 255, 255, 2, 255, 3, 255,
-    255, 255, 4, 255, 5, 255, 255, 255, 6, 255, 255, 255, 255, 255, 7};
-// number of R8 residues <= r
-static __constant__ unsigned char c_CNTLE30[30] = {
-    0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 4, 4,
-    4, 4, 5, 5, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7, 8};
-// distance from residue r to the next residue coprime to 30 (strictly greater)
-static __constant__ unsigned char c_NEXT30[30] = {
-    1, 6, 5, 4, 3, 2, 1, 4, 3, 2, 1, 2, 1, 4, 3,
-    2, 1, 2, 1, 4, 3, 2, 1, 6, 5, 4, 3, 2, 1, 2};
+// ------------------------------------------------------------- wheel residues
+// R8MASK has bit r set for the residues r mod 30 that are coprime to 30,
+// R8PACK holds R8[0..7] in 5-bit fields.  Everything below is bit
+// arithmetic, so lanes with different residues never serialize on a table.
+#define PC_R8MASK 0x208A2882u
+#define PC_R8PACK (1ull | 7ull << 5 | 11ull << 10 | 13ull << 15 | 17ull << 20 | 19ull << 25 | 23ull << 30 | 29ull << 35)
+
+__device__ __forceinline__ u32 r8(u32 j) { return (u32)(PC_R8PACK >> (5 * j)) & 31u; }            // R8[j]
+__device__ __forceinline__ bool coprime30(u32 r) { return (PC_R8MASK >> r) & 1u; }                  // gcd(r, 30) == 1
+__device__ __forceinline__ u32 cntle30(u32 r) { return __popc(PC_R8MASK & ((2u << r) - 1u)); }      // #R8 <= r
+__device__ __forceinline__ u32 idx30(u32 r) { return cntle30(r) - 1u; }                               // j with R8[j] == r
+__device__ __forceinline__ u32 next30(u32 r)                                                          // to next coprime > r
+{
+    const u32 m = PC_R8MASK >> (r + 1);
+    return m ? (u32)__ffs(m) : 31u - r;
+}
 
 // ------------------------------------------------------ exact integer roots
 PC_HD int pc_bitlen(u64 n) { int k = 0; while (n) { k++; n >>= 1; } return k; }
@@ -90,22 +92,30 @@ PC_HD u64 pc_max(u64 a, u64 b) { return a > b ? a : b; }
 
 // ----------------------------------------------------------- lookup tables
 // pi table: mod-30 bitset of the primes in [0, limit] (1 is cleared), one
-// u64 word per 240 numbers, plus pcnt[w] = number of set bits in words < w.
+// record per 240 numbers: the 64-bit word and the number of set bits in all
+// earlier words, so that one 16-byte load answers a lookup.
+struct __align__(16) PiRec {
+    u64 bits;
+    u32 cnt;
+    u32 pad;
+};
+
 struct PiTable {
-    const u64* words;
-    const u32* pcnt;
+    const PiRec* rec;
     u64 limit;
 };
 
 // pi(v) for 0 <= v <= limit.
 __device__ __forceinline__ u64 pi_lookup(const PiTable& t, u64 v)
 {
-    u64 small = (v >= 2) + (v >= 3) + (v >= 5);
-    u64 w = v / 240;
-    u32 r = (u32)(v - w * 240);
-    u32 e = 8 * (r / 30) + c_CNTLE30[r % 30];
-    u64 mask = e >= 64 ? ~0ull : ((1ull << e) - 1);
-    return small + t.pcnt[w] + __popcll(__ldg(t.words + w) & mask);
+    const u64 small = (v >= 2) + (v >= 3) + (v >= 5);
+    const u64 w = v / 240;
+    const u32 r = (u32)(v - w * 240);
+    const u32 e = 8 * (r / 30) + cntle30(r % 30);
+    const uint4 q = __ldg((const uint4*)(t.rec + w));
+    const u64 bits = (u64)q.x | ((u64)q.y << 32);
+    const u64 mask = e >= 64 ? ~0ull : ((1ull << e) - 1);
+    return small + q.z + __popcll(bits & mask);
 }
 
 // rank structure over a plain bitset of [0, limit]: rank(v) = #set bits <= v.

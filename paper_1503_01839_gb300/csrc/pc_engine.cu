@@ -75,7 +75,7 @@ extern "C" void pc_destroy(pc_ctx* ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     Tables& T = ctx->T;
-    DevBuf* bufs[] = {&T.small_primes, &T.pi_words, &T.pi_pcnt, &T.primes, &T.primes_rcp, &T.ml_m, &T.ml_info,
+    DevBuf* bufs[] = {&T.small_primes, &T.pi_rec, &T.primes, &T.primes_rcp, &T.ml_m, &T.ml_info,
                       &T.ml_gpf, &T.ml_rcp,
                       &T.rank_bits, &T.rank_cnt, &ctx->seg_b, &ctx->seg_off, &ctx->counts, &ctx->tallies,
                       &ctx->acc_seg, &ctx->partials, &ctx->result, &ctx->misc, &ctx->scan_tmp, &ctx->queue,

@@ -41,7 +41,7 @@
 #include "pc_sieve.cuh"
 
 static constexpr u32 BATCH = 64;
-static constexpr u32 EMAX = 64;        // multiples of one large prime in a segment (at most 48)
+static constexpr u32 EMAX = 48;        // multiples of one large prime in a segment (at most 48)
 static constexpr u32 RECOUNT_P = 128;   // below this a warp recounts its blocks after crossing off
 static constexpr u32 MAX_NW = 16;       // warps (sub-ranges) per segment
 static constexpr u32 MAX_SUB = 4096;    // bytes per sub-range: 32 blocks of 1024 bits
@@ -65,7 +65,9 @@ struct HardArgs {
     MList ml;
     const u32* primes;
     const u64* primes_rcp;
+    u64 rcp_y;          // floor((2^64 - 1) / y)
     const u32* segB;
+    const u64* rcp_seg;   // per segment: reciprocals of L_s and L_s + span (0 for L = 0)
     const u64* off;
     u32* counts;
     i32* tallies;
@@ -76,27 +78,32 @@ struct HardArgs {
     unsigned long long* stat;      // [0] hard leaves, [1] multiples crossed off
 };
 
-struct StepInfo {
+struct __align__(16) StepInfo {
     u64 xp;        // x / p_b
     u64 q;         // L / p_b
     u64 mlo, mhi;  // leaf window m in (mlo, mhi]
-    u16 coff[8];   // floor(p * R8[j] / 30): byte offset of class j inside a wheel round
-    u8 cbit[8];    // bit of class j inside its byte
+    u64 vp;        // floor((2^64 - 1) / p_b)
     u32 p;
     u32 r0;        // L mod p_b
+    u16 coff[8];   // floor(p * R8[j] / 30): byte offset of class j inside a wheel round
+    u8 cbit[8];    // bit of class j inside its byte
     u32 flags;     // bit 0: leaves are primes, bit 1: step has leaves, bit 2: cross off by events
     u32 ne;        // events (multiples of p_b in the segment), bit 2 only
     u32 pself;     // segment bit of p_b itself, or ~0
     u32 wmask;     // warps whose sub-range holds an event
+    u32 pad[2];
 };
 
-// leaf range of prime b in the segment [L, L + span): m in (mlo, mhi]
-__device__ __forceinline__ bool leaf_window(const HardArgs& A, u64 p, u64 xp, u64 L, u64& mlo, u64& mhi)
+// leaf range of prime b in the segment [L, L + span): m in (mlo, mhi].
+// vp, vL, vLs: reciprocals of p, L (0 when L = 0) and L + span.
+__device__ __forceinline__ bool leaf_window(const HardArgs& A, u64 p, u64 vp, u64 xp, u64 L, u64 vL, u64 vLs,
+                                            u64& mlo, u64& mhi)
 {
-    const u64 T = pc_min(p * p, A.y);     // hard: u >= min(p^2, y)
-    mhi = pc_min(A.y, xp / T);
-    if (L) mhi = pc_min(mhi, xp / L);     // u >= L
-    mlo = pc_max(A.y / p, xp / (L + A.span));   // u < L + span, and m > y / p
+    // hard: u >= min(p^2, y); xp / p^2 = floor(floor(xp / p) / p)
+    const u64 xT = p * p <= A.y ? div_rcp(div_rcp(xp, p, vp), p, vp) : div_rcp(xp, A.y, A.rcp_y);
+    mhi = pc_min(A.y, xT);
+    if (L) mhi = pc_min(mhi, div_rcp(xp, L, vL));                        // u >= L
+    mlo = pc_max(div_rcp(A.y, p, vp), div_rcp(xp, L + A.span, vLs));     // u < L + span, m > y / p
     return mhi > mlo;
 }
 
@@ -110,12 +117,14 @@ __device__ __forceinline__ bool leaf_window(const HardArgs& A, u64 p, u64 xp, u6
 __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const u32 nw = A.nw, sub_bytes = A.sub_bytes, sub_words = sub_bytes >> 2, nbw = sub_bytes >> 7;
+    // blocks of 256 bits (four 64-bit words); each lane owns bpl consecutive blocks
+    const u32 nw = A.nw, sub_bytes = A.sub_bytes, sub_words = sub_bytes >> 2, nbw = sub_bytes >> 5, bpl = nbw >> 5;
     const u32 sub_bits = sub_bytes << 3;
     StepInfo* st = (StepInfo*)smem_raw;
     u32* bits = (u32*)(smem_raw + BATCH * sizeof(StepInfo));
-    u32* blk = bits + (A.seg_bytes >> 2);          // nw * 32
-    u32* I = blk + nw * 32;                        // BATCH * (nw + 1)
+    u16* blk = (u16*)(bits + (A.seg_bytes >> 2));  // nw * nbw block counters
+    u16* pre = blk + nw * nbw;                     // nw * nbw prefix counts
+    u32* I = (u32*)(pre + nw * nbw);               // BATCH * (nw + 1)
     u32* cw = I + BATCH * (nw + 1);                // BATCH * nw
     i32* tw = (i32*)(cw + BATCH * nw);             // BATCH * nw
     i32* basew = tw + BATCH * nw;                  // BATCH * nw
@@ -124,6 +133,7 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
 
     __shared__ u32 patw[80];
     __shared__ u32 prev[MAX_NW];
+    __shared__ u64 rLk[MAX_NW + 1];   // reciprocals of L + k * dspan, k = 0..nw
     __shared__ u32 s_item;
     __shared__ i128 red[32];
 
@@ -131,6 +141,21 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
     make_pattern_words(patw, A.k0);
     u32* my = bits + w * sub_words;
     const u64* my64 = (const u64*)my;
+    u16* myblk = blk + w * nbw;
+    u32* myblk32 = (u32*)myblk;
+    u16* mypre = pre + w * nbw;
+    // count the set bits of this lane's blocks into myblk; returns the lane total
+    auto count_blocks = [&]() -> u32 {
+        u32 tot = 0;
+        for (u32 k = 0; k < bpl; k++) {
+            const u32 bi = lane * bpl + k;
+            const u32 c = __popcll(my64[4 * bi]) + __popcll(my64[4 * bi + 1]) + __popcll(my64[4 * bi + 2]) +
+                          __popcll(my64[4 * bi + 3]);
+            myblk[bi] = (u16)c;
+            tot += c;
+        }
+        return tot;
+    };
     i64 acc = 0;
     unsigned long long nleaves = 0, nclears = 0;
 
@@ -148,16 +173,13 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
         const u64 Lw = L + w * A.dspan;
 
         fill_pattern(bits, A.seg_bytes >> 2, L, patw, A.k0);
-        __syncthreads();
-        u32 cnt;
-        {
-            u32 c = 0;
-            if (lane < nbw)
-                for (u32 k = 0; k < 16; k++) c += __popcll(my64[lane * 16 + k]);
-            if (lane < nbw) blk[w * 32 + lane] = c;
-            cnt = __reduce_add_sync(0xffffffffu, c);
-            if (lane == 0) prev[w] = cnt;
+        if (tid <= nw) {
+            const u64 Lk = L + tid * A.dspan;
+            rLk[tid] = Lk ? ~0ull / Lk : 0;
         }
+        __syncthreads();
+        u32 cnt = __reduce_add_sync(0xffffffffu, count_blocks());
+        if (lane == 0) prev[w] = cnt;
         __syncthreads();
         if (tid == 0 && rep == 0) {
             u32 t = 0;
@@ -173,16 +195,19 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                 const u32 b = bb + t;
                 StepInfo si;
                 const u64 p = A.primes[b];
+                const u64 vp = A.primes_rcp[b];
                 si.p = (u32)p;
-                si.xp = A.x / p;
-                si.q = L / p;
+                si.vp = vp;
+                si.xp = div_rcp(A.x, p, vp);
+                si.q = div_rcp(L, p, vp);
                 si.r0 = (u32)(L - si.q * p);
+                si.pad[0] = si.pad[1] = 0;
                 si.flags = 0;
                 si.mlo = si.mhi = 0;
                 si.ne = 0;
                 si.wmask = 0;
                 si.pself = (p >= L && p < L + A.span) ? seg_pos(p, L) : ~0u;
-                if (b > A.kleaf && b <= A.a && leaf_window(A, p, si.xp, L, si.mlo, si.mhi))
+                if (b > A.kleaf && b <= A.a && leaf_window(A, p, vp, si.xp, L, rLk[0], rLk[nw], si.mlo, si.mhi))
                     si.flags = 2u | (p * p > A.y ? 1u : 0u);
                 for (int j = 0; j < 8; j++) {
                     si.coff[j] = 0;
@@ -202,7 +227,7 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                             const u32 pos = seg_pos(n, L);
                             ev[t * EMAX + ne++] = pos;
                             wm |= 1u << (pos >> A.sub_shift);
-                            const u32 d = c_NEXT30[r];
+                            const u32 d = next30(r);
                             r += d;
                             if (r >= 30) r -= 30;
                             n += p * d;
@@ -211,9 +236,9 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                         si.wmask = wm;
                     } else {
                         for (int j = 0; j < 8; j++) {
-                            const u32 pr = (u32)p * c_R8[j];
+                            const u32 pr = (u32)p * r8(j);
                             si.coff[j] = (u16)(pr / 30);
-                            si.cbit[j] = c_IDX30[pr % 30];
+                            si.cbit[j] = (u8)idx30(pr % 30);
                         }
                     }
                 }
@@ -229,7 +254,7 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                     u64 v;
                     if (k == 0) v = si.mhi;
                     else if (k == nw) v = si.mlo;
-                    else v = pc_max(pc_min(si.xp / (L + k * A.dspan), si.mhi), si.mlo);
+                    else v = pc_max(pc_min(div_rcp(si.xp, L + k * A.dspan, rLk[k]), si.mhi), si.mlo);
                     if (si.flags & 1u) {
                         const u64 b = bb + t;
                         v32 = (u32)(pc_min(pc_max(pi_lookup(A.pit, v), b), A.a) + 1);
@@ -244,7 +269,7 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                 const StepInfo& si = st[t];
                 if (si.flags & 4u || bb + t >= Bs) continue;
                 const u64 p = si.p;
-                u64 klo = si.q + (si.r0 + (u32)(k * A.dspan) + si.p - 1) / si.p;   // ceil(L_k / p)
+                u64 klo = si.q + div_rcp((u64)si.r0 + k * A.dspan + p - 1, p, si.vp);   // ceil(L_k / p)
                 if (klo < p) klo = p;
                 const u64 qa = klo / 30;
                 const i64 base = (i64)(p * qa) - (i64)(L / 30 + (u64)k * sub_bytes);
@@ -261,20 +286,27 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                     if (fl & 2u) {
                         u32 j0 = I[t * (nw + 1) + w + 1], j1 = I[t * (nw + 1) + w];
                         if (R > 1 && j1 > j0) {
-                            const u64 n = j1 - j0;
-                            const u32 a0 = j0 + (u32)(n * rep / R), a1 = j0 + (u32)(n * (rep + 1) / R);
+                            const u32 n = j1 - j0, chunk = (n + R - 1) / R;
+                            const u32 a0 = j0 + min(n, rep * chunk), a1 = j0 + min(n, (rep + 1) * chunk);
                             j0 = a0;
                             j1 = a1;
                         }
                         if (j1 > j0) {
-                            u32 pre = lane < nbw ? blk[w * 32 + lane] : 0;
-                            {
-                                u32 incl = pre;
+                            {   // prefix counts of the 256-bit blocks of the sub-range
+                                u32 run = 0;
+                                for (u32 k = 0; k < bpl; k++) run += myblk[lane * bpl + k];
+                                u32 incl = run;
                                 for (int o = 1; o < 32; o <<= 1) {
                                     u32 v = __shfl_up_sync(0xffffffffu, incl, o);
                                     if (lane >= o) incl += v;
                                 }
-                                pre = incl - pre;
+                                run = incl - run;
+                                for (u32 k = 0; k < bpl; k++) {
+                                    const u32 bi = lane * bpl + k;
+                                    mypre[bi] = (u16)run;
+                                    run += myblk[bi];
+                                }
+                                __syncwarp();
                             }
                             const u64 xp = st[t].xp;
                             for (u32 base = j0; base < j1; base += 32) {
@@ -295,14 +327,13 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                                     }
                                 }
                                 const u64 u = ok ? div_rcp(xp, m, v) : Lw;
-                                const u32 e = seg_count_end(u, Lw);
-                                u32 bi = e >> 10;
-                                if (bi >= nbw) bi = nbw - 1;
-                                const u32 pb = __shfl_sync(0xffffffffu, pre, bi);
                                 if (ok) {
-                                    u32 c = pb;
+                                    const u32 e = seg_count_end(u, Lw);
+                                    u32 bi = e >> 8;
+                                    if (bi >= nbw) bi = nbw - 1;
+                                    u32 c = mypre[bi];
                                     const u32 ew = e >> 6;
-                                    for (u32 ww = bi << 4; ww < ew; ww++) c += __popcll(my64[ww]);
+                                    for (u32 ww = bi << 2; ww < ew; ww++) c += __popcll(my64[ww]);
                                     if (e & 63) c += __popcll(my64[ew] & ((1ull << (e & 63)) - 1));
                                     acc += neg ? (i64)c : -(i64)c;
                                     tl += neg ? 1 : -1;
@@ -324,7 +355,7 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                         if (old & mask) {
                             my[pos >> 5] = old & ~mask;
                             dec++;
-                            if (!recount) atomicSub(&blk[w * 32 + (pos >> 10)], 1u);
+                            if (!recount) atomicSub(&myblk32[pos >> 9], 1u << (16 * ((pos >> 8) & 1)));
                         }
                     };
                     if (fl & 4u) {
@@ -358,7 +389,7 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                                 for (u32 r = o;; r += 4) {
                                     const i64 by = (i64)base + (i64)p * r + cj;
                                     if (by >= (i64)sub_bytes) break;
-                                    if (by < 0 || (r == 0 && c_R8[j] < kmod)) continue;
+                                    if (by < 0 || (r == 0 && r8(j) < kmod)) continue;
                                     clear_bit(((u32)by << 3) + bj);
                                     nclears++;
                                 }
@@ -370,7 +401,7 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                                         if (b0 >= (i64)sub_bytes) break;
 #pragma unroll
                                         for (int jj = 0; jj < 8; jj++) {
-                                            if (r == 0 && c_R8[jj] < kmod) continue;
+                                            if (r == 0 && r8(jj) < kmod) continue;
                                             const i64 by = b0 + (i64)((cw4[jj >> 1] >> (16 * (jj & 1))) & 0xFFFFu);
                                             if (by >= (i64)sub_bytes) break;
                                             if (by < 0) continue;
@@ -389,11 +420,7 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                     if (lane == 0 && ps != ~0u && (ps >> A.sub_shift) == w) clear_bit(ps & (sub_bits - 1));
                     if (recount) {
                         __syncwarp();
-                        u32 c = 0;
-                        if (lane < nbw)
-                            for (u32 k = 0; k < 16; k++) c += __popcll(my64[lane * 16 + k]);
-                        if (lane < nbw) blk[w * 32 + lane] = c;
-                        cnt = __reduce_add_sync(0xffffffffu, c);
+                        cnt = __reduce_add_sync(0xffffffffu, count_blocks());
                     } else {
                         cnt -= __reduce_add_sync(0xffffffffu, dec);
                     }
@@ -437,10 +464,12 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
 }
 
 // ---------------------------------------------------------- schedule
-__global__ void seg_b_kernel(u64 x, u64 nseg, u64 span, u32 bmax, PiTable pit, u32* segB)
+__global__ void seg_b_kernel(u64 x, u64 nseg, u64 span, u32 bmax, PiTable pit, u32* segB, u64* rcp_seg)
 {
     u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg) return;
+    rcp_seg[2 * s] = s ? ~0ull / (s * span) : 0;
+    rcp_seg[2 * s + 1] = ~0ull / ((s + 1) * span);
     u32 B = bmax;
     if (s > 0) {
         u64 L = s * span;
@@ -480,9 +509,10 @@ __global__ void hard_estimate_kernel(HardArgs A, u64 total, u32 nrows, unsigned 
         const u64 s = e - A.off[lo];
         const u64 L = s * A.span;
         const u64 p = A.primes[b];
-        const u64 xp = A.x / p;
+        const u64 vp = A.primes_rcp[b];
+        const u64 xp = div_rcp(A.x, p, vp);
         u64 mlo, mhi;
-        if (!leaf_window(A, p, xp, L, mlo, mhi)) continue;
+        if (!leaf_window(A, p, vp, xp, L, A.rcp_seg[2 * s], A.rcp_seg[2 * s + 1], mlo, mhi)) continue;
         u64 n;
         if (p * p > A.y) {
             const u64 k0 = pc_min(pc_max(pi_lookup(A.pit, mlo), b), A.a);
@@ -628,12 +658,16 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 
     const u64 nrows = bmax - A.k0 + 1;
     PC_TRY(buf_reserve(ctx, ctx->seg_b, A.nseg * sizeof(u32) + (nrows + 1) * sizeof(u32)));
-    PC_TRY(buf_reserve(ctx, ctx->seg_off, (nrows + 1) * sizeof(u64) + A.nseg * sizeof(u64)));
+    PC_TRY(buf_reserve(ctx, ctx->seg_off, (nrows + 1) * sizeof(u64) + 3 * A.nseg * sizeof(u64)));
     u32* segB = ctx->seg_b.as<u32>();
     u32* rowlen = segB + A.nseg;
     u64* off = ctx->seg_off.as<u64>();
     unsigned long long* est = (unsigned long long*)(off + nrows + 1);
-    seg_b_kernel<<<(unsigned)((A.nseg + 255) / 256), 256, 0, ctx->stream>>>(P.x, A.nseg, A.span, A.bmax, A.pit, segB);
+    u64* rcp_seg = (u64*)(est + A.nseg);
+    A.rcp_seg = rcp_seg;
+    A.rcp_y = ~0ull / P.y;
+    seg_b_kernel<<<(unsigned)((A.nseg + 255) / 256), 256, 0, ctx->stream>>>(P.x, A.nseg, A.span, A.bmax, A.pit, segB,
+                                                                            rcp_seg);
     PC_LAUNCHED(ctx);
     row_len_kernel<<<(unsigned)((nrows + 255) / 256), 256, 0, ctx->stream>>>(segB, A.nseg, A.k0, A.bmax, rowlen);
     PC_LAUNCHED(ctx);
@@ -657,7 +691,8 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 
     const u32 nbw = A.sub_bytes >> 7;
     (void)nbw;
-    const size_t smem = BATCH * sizeof(StepInfo) + A.seg_bytes + (size_t)A.nw * 32 * 4 +
+    static_assert(sizeof(StepInfo) % 16 == 0, "StepInfo must keep 16-byte alignment");
+    const size_t smem = BATCH * sizeof(StepInfo) + A.seg_bytes + (size_t)A.nw * (A.sub_bytes >> 5) * 4 +
                         (size_t)BATCH * (A.nw + 1) * 4 + 3 * (size_t)BATCH * A.nw * 4 + (size_t)BATCH * EMAX * 4 +
                         (size_t)BATCH * A.nw;
     int per_sm = ctx->params.ctas_per_sm ? (int)ctx->params.ctas_per_sm : 0;

@@ -51,7 +51,7 @@ struct Tables {
     u32 n_small = 0;
     // pi table over [0, pi_limit]
     u64 pi_limit = 0;
-    DevBuf pi_words, pi_pcnt;
+    DevBuf pi_rec;   // PiRec per 240 numbers
     // primes[1..nprimes] (u32), primes[0] = 1, primes[nprimes+1] = next prime
     u64 prime_limit = 0;
     u64 nprimes = 0;
@@ -66,7 +66,7 @@ struct Tables {
     DevBuf phiT[8];
     bool phiT_ok[8] = {false, false, false, false, false, false, false, false};
 
-    PiTable pi() const { return PiTable{pi_words.as<u64>(), pi_pcnt.as<u32>(), pi_limit}; }
+    PiTable pi() const { return PiTable{pi_rec.as<PiRec>(), pi_limit}; }
     RankTable rank() const { return RankTable{rank_bits.as<u64>(), rank_cnt.as<u32>(), ml_limit}; }
     MList mlist() const
     {

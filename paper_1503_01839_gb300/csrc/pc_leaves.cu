@@ -23,6 +23,7 @@ struct LeafArgs {
     RankTable rk;
     MList ml;
     const u32* primes;
+    const u64* primes_rcp;   // floor((2^64 - 1) / p_k)
     u64 n_lim;   // list entries with m <= y: [0, n_lim)
 };
 
@@ -38,6 +39,7 @@ static LeafArgs make_args(pc_ctx* ctx, const LeafProblem& P, u64 n_lim)
     A.rk = ctx->T.rank();
     A.ml = ctx->T.mlist();
     A.primes = ctx->T.primes.as<u32>();
+    A.primes_rcp = ctx->T.primes_rcp.as<u64>();
     A.n_lim = n_lim;
     return A;
 }
@@ -183,41 +185,52 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, u64 nb, const EasyRange* rng, 
     __shared__ i128 scratch[32];
     __shared__ u64 s_b;
     i64 s = 0;
-    for (u64 ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        if (threadIdx.x == 0) {
-            // largest t with choff[t] <= ch
-            u64 lo = 0, hi = nb;
-            while (hi - lo > 1) {
-                u64 mid = (lo + hi) >> 1;
-                if (choff[mid] <= ch) lo = mid; else hi = mid;
-            }
-            s_b = lo;
+    // a contiguous run of chunks per CTA: one search, then a linear walk over b
+    const u64 per = (nchunks + gridDim.x - 1) / gridDim.x;
+    const u64 ch0 = (u64)blockIdx.x * per, ch1 = pc_min(nchunks, ch0 + per);
+    if (threadIdx.x == 0 && ch0 < ch1) {
+        u64 lo = 0, hi = nb;   // largest t with choff[t] <= ch0
+        while (hi - lo > 1) {
+            u64 mid = (lo + hi) >> 1;
+            if (choff[mid] <= ch0) lo = mid; else hi = mid;
         }
-        __syncthreads();
-        u64 t = s_b;
-        __syncthreads();
+        s_b = lo;
+    }
+    __syncthreads();
+    u64 t = s_b;
+    for (u64 ch = ch0; ch < ch1; ch++) {
+        while (t + 1 < nb && choff[t + 1] <= ch) t++;
         u64 b = b_lo + t;
         EasyRange r = rng[t];
         u64 start = r.i0 + (ch - choff[t]) * EASY_CHUNK;
         u64 end = pc_min(r.i1, start + EASY_CHUNK);
         u64 p = A.primes[b];
-        u64 xp = A.x / p;
+        u64 xp = div_rcp(A.x, p, A.primes_rcp[b]);
         for (u64 i = start + threadIdx.x; i < end; i += blockDim.x) {
-            u64 m;
-            bool neg;
+            u64 m, v;
+            bool neg = true;
             if (r.src) {
                 m = A.primes[i];
-                neg = true;
+                v = A.primes_rcp[i];
             } else {
-                u32 info = A.ml.info[i];
+                const u32 info = A.ml.info[i];
                 if ((info >> 1) <= b) continue;
                 if (A.trunc && A.ml.gpf[i] > A.a) continue;
                 m = A.ml.m[i];
+                v = A.ml.rcp[i];
                 neg = info & 1;
             }
-            u64 u = xp / m;
-            i64 v = (i64)pi_lookup(A.pit, u) - (i64)b + 2;
-            s += neg ? v : -v;
+            // easy: p_b <= u < y < 2^32; for b > 3, u >= 7 and pi(u) counts 2, 3, 5
+            const u32 u = (u32)div_rcp(xp, m, v);
+            const u32 w = u / 240, rr = u - w * 240;
+            const u32 e = 8 * (rr / 30) + cntle30(rr % 30);   // 0..64
+            const uint4 q = __ldg((const uint4*)(A.pit.rec + w));
+            u32 c;
+            if (e <= 32) c = __popc(q.x & (e == 32 ? ~0u : (1u << e) - 1u));
+            else c = __popc(q.x) + __popc(q.y & (e == 64 ? ~0u : (1u << (e - 32)) - 1u));
+            const u32 small = b > 3 ? 3u : (u >= 2) + (u >= 3) + (u >= 5);
+            const i64 t2 = (i64)(small + q.z + c) - (i64)b + 2;
+            s += neg ? t2 : -t2;
         }
     }
     i128 v = block_sum_i128((i128)s, scratch);

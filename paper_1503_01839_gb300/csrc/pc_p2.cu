@@ -20,6 +20,7 @@ struct P2Args {
     u64 span;
     PiTable pit;
     const u32* primes;
+    const u64* primes_rcp;   // floor((2^64 - 1) / p_b)
     u32* cnt;         // set bits per segment (final state)
     u32* tally;       // number of p answered per segment
     I128Pair* acc;    // sum of local counts per segment
@@ -59,13 +60,13 @@ __global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A)
         for (; b <= A.B; b++) {
             const u64 p = A.primes[b];
             if (p * 8 > A.seg_bytes) break;
-            u64 ks = L ? (L + p - 1) / p : 0;
+            u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[b]) : 0;
             if (ks < p) ks = p;
             cross_off_coop(bits, A.seg_bytes, L, (u32)p, ks, tid, NT, none);
         }
         for (u32 bb = b + tid; bb <= A.B; bb += NT) {
             const u64 p = A.primes[bb];
-            u64 ks = L ? (L + p - 1) / p : 0;
+            u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[bb]) : 0;
             if (ks < p) ks = p;
             cross_off_single(bits, A.seg_bytes, L, (u32)p, ks, none);
         }
@@ -123,11 +124,11 @@ __global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A)
         if (phi > plo) {
             const u64 w0 = (plo + 1) / 240, w1 = phi / 240;
             for (u64 w = w0 + tid; w <= w1; w += NT) {
-                u64 v = __ldg(A.pit.words + w);
+                u64 v = A.pit.rec[w].bits;
                 while (v) {
                     int bi = __ffsll((long long)v) - 1;
                     v &= v - 1;
-                    u64 p = 240 * w + 30 * (u64)(bi >> 3) + c_R8[bi & 7];
+                    u64 p = 240 * w + 30 * (u64)(bi >> 3) + r8(bi & 7);
                     if (p <= plo || p > phi) continue;
                     u64 q = A.x / p;
                     u32 e = seg_count_end(q, L);
@@ -237,6 +238,7 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     A.nseg = z / A.span + 1;
     A.pit = ctx->T.pi();
     A.primes = ctx->T.primes.as<u32>();
+    A.primes_rcp = ctx->T.primes_rcp.as<u64>();
     PC_TRY(buf_reserve(ctx, ctx->counts, A.nseg * 2 * sizeof(u32)));
     PC_TRY(buf_reserve(ctx, ctx->acc_seg, A.nseg * sizeof(I128Pair)));
     PC_TRY(buf_reserve(ctx, ctx->queue, 64));

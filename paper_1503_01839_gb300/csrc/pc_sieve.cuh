@@ -14,7 +14,7 @@
 __device__ __forceinline__ u64 coprime30_at_or_after(u64 k0)
 {
     u32 r = (u32)(k0 % 30);
-    return c_IDX30[r] != 255 ? k0 : k0 + c_NEXT30[r];
+    return coprime30(r) ? k0 : k0 + next30(r);
 }
 
 // Cooperative cross-off of the multiples k*p, k >= kstart, k coprime to 30,
@@ -29,10 +29,10 @@ __device__ __forceinline__ u32 cross_off_coop(u32* bits, u32 seg_bytes, u64 L, u
     const int j = t & 7;
     const u32 rounds = (u32)nt >> 3;
     const u32 o = (u32)t >> 3;
-    const u32 rj = c_R8[j];
+    const u32 rj = r8(j);
     const u64 q0 = kstart / 30;
     const u32 pr = p * rj;                 // p < 2^27 here, so no overflow
-    const u32 bit = c_IDX30[pr % 30];
+    const u32 bit = idx30(pr % 30);
     const u64 Lb = L / 30;
     // byte(q) = p*q + pr/30 - L/30 for k = 30*q + rj
     u64 q = q0 + o;
@@ -64,11 +64,11 @@ __device__ __forceinline__ void cross_off_single(u32* bits, u32 seg_bytes, u64 L
     u64 n = (u64)p * k;
     while (n < end) {
         u32 rel = (u32)(n - L);
-        u32 pos = (rel / 30) * 8 + c_IDX30[rel % 30];
+        u32 pos = (rel / 30) * 8 + idx30(rel % 30);
         u32 mask = 1u << (pos & 31);
         u32 old = atomicAnd(&bits[pos >> 5], ~mask);
         if (old & mask) newly(pos);
-        u32 d = c_NEXT30[r];
+        u32 d = next30(r);
         r += d;
         if (r >= 30) r -= 30;
         n += (u64)p * d;
@@ -79,7 +79,7 @@ __device__ __forceinline__ void cross_off_single(u32* bits, u32 seg_bytes, u64 L
 __device__ __forceinline__ u32 seg_pos(u64 n, u64 L)
 {
     u32 rel = (u32)(n - L);
-    return (rel / 30) * 8 + c_IDX30[rel % 30];
+    return (rel / 30) * 8 + idx30(rel % 30);
 }
 
 // Number of bits before the first bit of integers > v, i.e. the count end
@@ -87,7 +87,7 @@ __device__ __forceinline__ u32 seg_pos(u64 n, u64 L)
 __device__ __forceinline__ u32 seg_count_end(u64 v, u64 L)
 {
     u32 rel = (u32)(v - L);
-    return (rel / 30) * 8 + c_CNTLE30[rel % 30];
+    return (rel / 30) * 8 + cntle30(rel % 30);
 }
 
 // Byte value of the wheel pattern of the primes 7 (depth 4) or 7 and 11
@@ -98,12 +98,12 @@ __device__ __forceinline__ u32 pattern_byte(u64 g, int depth)
     if (depth >= 4) {
         u32 r7 = (u32)(g % 7);
         for (int j = 0; j < 8; j++)
-            if ((30 * r7 + c_R8[j]) % 7 == 0) v &= ~(1u << j);
+            if ((30 * r7 + r8(j)) % 7 == 0) v &= ~(1u << j);
     }
     if (depth >= 5) {
         u32 r11 = (u32)(g % 11);
         for (int j = 0; j < 8; j++)
-            if ((30 * r11 + c_R8[j]) % 11 == 0) v &= ~(1u << j);
+            if ((30 * r11 + r8(j)) % 11 == 0) v &= ~(1u << j);
     }
     return v;
 }

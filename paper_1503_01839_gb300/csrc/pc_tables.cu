@@ -102,7 +102,7 @@ __global__ void pi_sieve_kernel(const u32* sp, u32 nsp, u64 limit, u64 nwords64,
 
 // ------------------------------------------------------------- primes[]
 // primes[k] = p_k for 1 <= k <= n_out; primes[0] = 1.
-__global__ void extract_primes_kernel(const u64* words, const u32* pcnt, u64 nwords, u32* primes, u64 n_out)
+__global__ void extract_primes_kernel(const PiRec* rec, u64 nwords, u32* primes, u64 n_out)
 {
     u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (w == 0) {
@@ -112,14 +112,14 @@ __global__ void extract_primes_kernel(const u64* words, const u32* pcnt, u64 nwo
         if (n_out >= 3) primes[3] = 5;
     }
     if (w >= nwords) return;
-    u64 v = words[w];
-    u64 idx = 3 + pcnt[w];
+    u64 v = rec[w].bits;
+    u64 idx = 3 + rec[w].cnt;
     while (v) {
         int b = __ffsll((long long)v) - 1;
         v &= v - 1;
         idx++;
         if (idx > n_out) return;
-        u64 n = 240 * w + 30 * (u64)(b >> 3) + c_R8[b & 7];
+        u64 n = 240 * w + 30 * (u64)(b >> 3) + r8(b & 7);
         primes[idx] = (u32)n;
     }
 }
@@ -277,35 +277,53 @@ static int ensure_small(pc_ctx* ctx)
     return PC_OK;
 }
 
+__global__ void pack_pi_kernel(const u64* words, const u32* pcnt, u64 n, PiRec* rec)
+{
+    u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < n) {
+        PiRec r;
+        r.bits = words[w];
+        r.cnt = pcnt[w];
+        r.pad = 0;
+        rec[w] = r;
+    }
+}
+
 static int build_pi(pc_ctx* ctx, u64 limit)
 {
     Tables& T = ctx->T;
     u64 nwords = limit / 240 + 1;
     u64 nseg = (limit + 30ull * PI_SEG_BYTES) / (30ull * PI_SEG_BYTES);
     u64 nw_alloc = nseg * (PI_SEG_BYTES / 8);
-    PC_TRY(buf_reserve(ctx, T.pi_words, nw_alloc * sizeof(u64)));
-    PC_TRY(buf_reserve(ctx, T.pi_pcnt, (nw_alloc + 1) * sizeof(u32)));
-    PC_TRY(buf_reserve(ctx, ctx->scan_tmp, 16));
-    DevBuf tmp;
-    int rc = buf_reserve(ctx, tmp, (nwords + 1) * sizeof(u32));
-    if (rc) return rc;
-    pi_sieve_kernel<<<(unsigned)nseg, 256, 0, ctx->stream>>>(T.small_primes.as<u32>(), T.n_small, limit, nwords,
-                                                            T.pi_words.as<u64>(), tmp.as<u32>());
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) rc = scan_exclusive_u32_to_u32(ctx, tmp.as<u32>(), T.pi_pcnt.as<u32>(), nwords);
-    else {
-        pc_set_error(ctx, "pi_sieve_kernel launch: %s", cudaGetErrorString(e));
-        rc = PC_ECUDA;
-    }
+    PC_TRY(buf_reserve(ctx, T.pi_rec, nwords * sizeof(PiRec)));
+    DevBuf words, cnt, pcnt;
+    int rc = buf_reserve(ctx, words, nw_alloc * sizeof(u64));
+    if (rc == PC_OK) rc = buf_reserve(ctx, cnt, (nwords + 1) * sizeof(u32));
+    if (rc == PC_OK) rc = buf_reserve(ctx, pcnt, (nwords + 1) * sizeof(u32));
     if (rc == PC_OK) {
-        e = cudaStreamSynchronize(ctx->stream);
-        if (e != cudaSuccess) {
-            pc_set_error(ctx, "pi table build: %s", cudaGetErrorString(e));
+        pi_sieve_kernel<<<(unsigned)nseg, 256, 0, ctx->stream>>>(T.small_primes.as<u32>(), T.n_small, limit, nwords,
+                                                                words.as<u64>(), cnt.as<u32>());
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) rc = scan_exclusive_u32_to_u32(ctx, cnt.as<u32>(), pcnt.as<u32>(), nwords);
+        else {
+            pc_set_error(ctx, "pi_sieve_kernel launch: %s", cudaGetErrorString(e));
             rc = PC_ECUDA;
         }
+        if (rc == PC_OK) {
+            pack_pi_kernel<<<(unsigned)((nwords + 255) / 256), 256, 0, ctx->stream>>>(
+                words.as<u64>(), pcnt.as<u32>(), nwords, T.pi_rec.as<PiRec>());
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) {
+                pc_set_error(ctx, "pi table build: %s", cudaGetErrorString(e));
+                rc = PC_ECUDA;
+            }
+        }
     }
-    buf_free(tmp);
-    ctx->stats.kernel_launches++;
+    buf_free(words);
+    buf_free(cnt);
+    buf_free(pcnt);
+    ctx->stats.kernel_launches += 2;
     if (rc == PC_OK) T.pi_limit = limit;
     return rc;
 }
@@ -323,7 +341,7 @@ static int build_primes(pc_ctx* ctx, u64 prime_limit)
     u64 wmax = T.pi_limit / 240 + 1;
     if (wlim > wmax) wlim = wmax;
     extract_primes_kernel<<<(unsigned)((wlim + 255) / 256), 256, 0, ctx->stream>>>(
-        T.pi_words.as<u64>(), T.pi_pcnt.as<u32>(), wlim, T.primes.as<u32>(), n_out);
+        T.pi_rec.as<PiRec>(), wlim, T.primes.as<u32>(), n_out);
     PC_LAUNCHED(ctx);
     PC_TRY(buf_reserve(ctx, T.primes_rcp, (n_out + 2) * sizeof(u64)));
     reciprocal_kernel<<<(unsigned)((n_out + 1 + 255) / 256), 256, 0, ctx->stream>>>(T.primes.as<u32>(), n_out + 1,
