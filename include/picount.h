@@ -53,14 +53,17 @@ typedef struct pc_i128 {
  * None of them changes any result. */
 typedef struct pc_params {
     uint32_t seg_bytes;   /* bytes of shared-memory bitset per sieve segment:
-                             1024, 2048, or a multiple of 4096 up to 65536;
+                             1024, 2048, or a multiple of 4096 up to 131072;
                              one byte holds 30 consecutive integers (mod-30
-                             wheel); one warp per 4096 bytes */
+                             wheel) */
     uint32_t ctas_per_sm; /* resident sieve CTAs per SM (1..4) */
-    uint32_t threads;     /* reserved (the sieve uses one warp per 4 KiB) */
+    uint32_t threads;     /* reserved (the sieve uses one warp per warp_bytes) */
     uint32_t alpha;       /* default alpha of pc_pi_count (y = alpha*iroot3(x)) */
     uint32_t c;           /* default wheel depth c of pc_pi_count (0..7) */
-    uint32_t reserved[3];
+    uint32_t warp_bytes;  /* bytes of a segment each warp of the hard-leaf sieve
+                             owns: 1024, 2048, 4096 or 8192, and at most 16
+                             warps per segment */
+    uint32_t reserved[2];
 } pc_params;
 
 /* Counters and phase times of the last successful call. */
@@ -74,6 +77,8 @@ typedef struct pc_stats {
     uint64_t steps;         /* (segment, prime) steps of the hard-leaf sieve */
     uint64_t hard_leaves;   /* hard special leaves resolved by the sieve */
     uint64_t clears;        /* multiples crossed off by the hard-leaf sieve */
+    uint64_t work_items;    /* sieve work items (segments, heavy ones split into replicas) */
+    uint64_t item_steps;    /* (work item, prime) steps actually run, replicas included */
     uint64_t kernel_launches;
     double ms_tables, ms_s1, ms_trivial, ms_easy, ms_hard, ms_p2, ms_total;
     double ms_hard_sieve;   /* the segmented sieve kernel alone (CUDA events) */

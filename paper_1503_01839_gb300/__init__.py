@@ -31,14 +31,15 @@ class PcI128(ctypes.Structure):
 
 class PcParams(ctypes.Structure):
     _fields_ = [("seg_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("threads", ctypes.c_uint32),
-                ("alpha", ctypes.c_uint32), ("c", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("alpha", ctypes.c_uint32), ("c", ctypes.c_uint32), ("warp_bytes", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class PcStats(ctypes.Structure):
     _fields_ = [("x", ctypes.c_uint64), ("y", ctypes.c_uint64), ("z", ctypes.c_uint64), ("a", ctypes.c_uint64),
                 ("B", ctypes.c_uint64), ("c", ctypes.c_uint32), ("seg_bytes", ctypes.c_uint32),
                 ("segments", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("hard_leaves", ctypes.c_uint64),
-                ("clears", ctypes.c_uint64),
+                ("clears", ctypes.c_uint64), ("work_items", ctypes.c_uint64), ("item_steps", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64),
                 ("ms_tables", ctypes.c_double), ("ms_s1", ctypes.c_double), ("ms_trivial", ctypes.c_double),
                 ("ms_easy", ctypes.c_double), ("ms_hard", ctypes.c_double), ("ms_p2", ctypes.c_double),
@@ -97,9 +98,9 @@ class Context:
     """One library context (device tables + scratch) on one CUDA device."""
 
     def __init__(self, device: int = 0, seg_bytes: int = 0, ctas_per_sm: int = 0, threads: int = 0,
-                 alpha: int = 0, c: int = 0):
+                 alpha: int = 0, c: int = 0, warp_bytes: int = 0):
         self._L = lib()
-        prm = PcParams(seg_bytes, ctas_per_sm, threads, alpha, c)
+        prm = PcParams(seg_bytes, ctas_per_sm, threads, alpha, c, warp_bytes)
         h = ctypes.c_void_p()
         rc = self._L.pc_create(ctypes.byref(h), device, ctypes.byref(prm))
         if rc != PC_OK:

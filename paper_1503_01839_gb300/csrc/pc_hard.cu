@@ -44,7 +44,8 @@ static constexpr u32 BATCH = 64;
 static constexpr u32 EMAX = 48;        // multiples of one large prime in a segment (at most 48)
 static constexpr u32 RECOUNT_P = 128;   // below this a warp recounts its blocks after crossing off
 static constexpr u32 MAX_NW = 16;       // warps (sub-ranges) per segment
-static constexpr u32 MAX_SUB = 4096;    // bytes per sub-range: 32 blocks of 1024 bits
+static constexpr u32 MAX_SUB = 8192;    // bytes per sub-range: up to 256 blocks of 256 bits
+static constexpr u32 MAX_SEG = 131072;  // bytes per segment
 
 struct HardItem {
     u32 s;    // segment
@@ -91,7 +92,8 @@ struct __align__(16) StepInfo {
     u32 ne;        // events (multiples of p_b in the segment), bit 2 only
     u32 pself;     // segment bit of p_b itself, or ~0
     u32 wmask;     // warps whose sub-range holds an event
-    u32 pad[2];
+    u32 row;       // off[b - k0]: start of the count / tally rows of b
+    u32 pad;
 };
 
 // leaf range of prime b in the segment [L, L + span): m in (mlo, mhi].
@@ -114,7 +116,7 @@ __device__ __forceinline__ bool leaf_window(const HardArgs& A, u64 p, u64 vp, u6
 // segment; the CTA lists them once per batch ("events") and each warp applies
 // those in its sub-range.  Multiples of one prime are >= p integers apart, so
 // lanes never share a word there either.
-__global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
+__global__ void __launch_bounds__(512, 1) hard_sieve_kernel(HardArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // blocks of 256 bits (four 64-bit words); each lane owns bpl consecutive blocks
@@ -201,7 +203,8 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                 si.xp = div_rcp(A.x, p, vp);
                 si.q = div_rcp(L, p, vp);
                 si.r0 = (u32)(L - si.q * p);
-                si.pad[0] = si.pad[1] = 0;
+                si.row = (u32)A.off[b - A.k0];
+                si.pad = 0;
                 si.flags = 0;
                 si.mlo = si.mhi = 0;
                 si.ne = 0;
@@ -277,71 +280,136 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                 kmodw[idx] = (u8)(klo - 30 * qa);
             }
             __syncthreads();
-            // C: every warp runs the batch over its own sub-range
-            for (u32 t = 0; t < nb; t++) {
+            // C: every warp runs the batch over its own sub-range.  Steps that touch
+            // neither its leaves nor its integers are skipped: the warp marks its
+            // busy steps with two ballots and fills the skipped counts afterwards.
+            auto leaf_range = [&](u32 t, u32& j0, u32& j1) {
+                j0 = I[t * (nw + 1) + w + 1];
+                j1 = I[t * (nw + 1) + w];
+                if (R > 1 && j1 > j0) {
+                    const u32 n = j1 - j0, chunk = (n + R - 1) / R;
+                    const u32 a0 = j0 + min(n, rep * chunk), a1 = j0 + min(n, (rep + 1) * chunk);
+                    j0 = a0;
+                    j1 = a1;
+                }
+            };
+            u64 busy = 0, leafy = 0;
+            u32 lj0[BATCH / 32], lj1[BATCH / 32];   // leaf range of step h*32 + lane
+#pragma unroll
+            for (u32 h = 0; h < BATCH / 32; h++) {
+                const u32 t = h * 32 + lane;
+                bool on = false;
+                lj0[h] = lj1[h] = 0;
+                if (t < nb) {
+                    const u32 b = bb + t, fl = st[t].flags, ps = st[t].pself;
+                    if (b < Bs) {
+                        if (!(fl & 4u) || ((st[t].wmask >> w) & 1u)) on = true;
+                        if (ps != ~0u && (ps >> A.sub_shift) == w) on = true;
+                    }
+                    if (b > A.kleaf && (fl & 2u)) {
+                        leaf_range(t, lj0[h], lj1[h]);
+                        if (lj1[h] > lj0[h]) on = true;
+                    }
+                    if (b > A.kleaf) tw[t * nw + w] = 0;
+                }
+                busy |= (u64)__ballot_sync(0xffffffffu, on) << (h * 32);
+                leafy |= (u64)__ballot_sync(0xffffffffu, lj1[h] > lj0[h]) << (h * 32);
+            }
+            // Leaf data (m, its reciprocal, lpf index and mu) does not depend on the
+            // sieve, so the first 32 leaves of the next leaf step are loaded ahead,
+            // while the warp is still crossing off earlier primes.
+            u32 pf_info = 0, pf_m = 0, pf_gpf = 0;
+            u64 pf_v = 0;
+            auto leaf_bounds = [&](u32 t, u32& j0, u32& j1) {
+                const u32 h = t >> 5;
+                j0 = __shfl_sync(0xffffffffu, h ? lj0[1] : lj0[0], t & 31);
+                j1 = __shfl_sync(0xffffffffu, h ? lj1[1] : lj1[0], t & 31);
+            };
+            auto prefetch = [&](u32 t) {
+                u32 j0, j1;
+                leaf_bounds(t, j0, j1);
+                const u32 i = j0 + lane;
+                pf_m = 0;
+                if (i < j1) {
+                    if (st[t].flags & 1u) {
+                        pf_info = ~0u;   // a prime: lpf = itself, mu = -1
+                        pf_m = A.primes[i];
+                        pf_v = A.primes_rcp[i];
+                        pf_gpf = 0;
+                    } else {
+                        pf_info = A.ml.info[i];
+                        pf_m = A.ml.m[i];
+                        pf_v = A.ml.rcp[i];
+                        pf_gpf = A.trunc ? A.ml.gpf[i] : 0;
+                    }
+                }
+            };
+            if (leafy) prefetch(__ffsll((long long)leafy) - 1);
+            __syncwarp();
+            const u32 cnt0 = cnt;
+            for (u64 todo = busy; todo; todo &= todo - 1) {
+                const u32 t = __ffsll((long long)todo) - 1;
                 const u32 b = bb + t;
                 const u32 fl = st[t].flags;
                 if (b > A.kleaf) {
                     int tl = 0;
-                    if (fl & 2u) {
-                        u32 j0 = I[t * (nw + 1) + w + 1], j1 = I[t * (nw + 1) + w];
-                        if (R > 1 && j1 > j0) {
-                            const u32 n = j1 - j0, chunk = (n + R - 1) / R;
-                            const u32 a0 = j0 + min(n, rep * chunk), a1 = j0 + min(n, (rep + 1) * chunk);
-                            j0 = a0;
-                            j1 = a1;
-                        }
-                        if (j1 > j0) {
-                            {   // prefix counts of the 256-bit blocks of the sub-range
-                                u32 run = 0;
-                                for (u32 k = 0; k < bpl; k++) run += myblk[lane * bpl + k];
-                                u32 incl = run;
-                                for (int o = 1; o < 32; o <<= 1) {
-                                    u32 v = __shfl_up_sync(0xffffffffu, incl, o);
-                                    if (lane >= o) incl += v;
-                                }
-                                run = incl - run;
-                                for (u32 k = 0; k < bpl; k++) {
-                                    const u32 bi = lane * bpl + k;
-                                    mypre[bi] = (u16)run;
-                                    run += myblk[bi];
-                                }
-                                __syncwarp();
+                    if ((leafy >> t) & 1u) {
+                        u32 j0, j1;
+                        leaf_bounds(t, j0, j1);
+                        {   // prefix counts of the 256-bit blocks of the sub-range
+                            u32 run = 0;
+                            for (u32 k = 0; k < bpl; k++) run += myblk[lane * bpl + k];
+                            u32 incl = run;
+                            for (int o = 1; o < 32; o <<= 1) {
+                                u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o) incl += v;
                             }
-                            const u64 xp = st[t].xp;
-                            for (u32 base = j0; base < j1; base += 32) {
-                                const u32 i = base + lane;
-                                bool ok = i < j1;
-                                u64 m = 1, v = ~0ull;
-                                bool neg = true;
-                                if (ok) {
-                                    if (fl & 1u) {
-                                        m = A.primes[i];
-                                        v = A.primes_rcp[i];
-                                    } else {
-                                        const u32 info = A.ml.info[i];
-                                        ok = (info >> 1) > b && !(A.trunc && A.ml.gpf[i] > A.a);
-                                        m = A.ml.m[i];
-                                        v = A.ml.rcp[i];
-                                        neg = info & 1u;
-                                    }
-                                }
-                                const u64 u = ok ? div_rcp(xp, m, v) : Lw;
-                                if (ok) {
-                                    const u32 e = seg_count_end(u, Lw);
-                                    u32 bi = e >> 8;
-                                    if (bi >= nbw) bi = nbw - 1;
-                                    u32 c = mypre[bi];
-                                    const u32 ew = e >> 6;
-                                    for (u32 ww = bi << 2; ww < ew; ww++) c += __popcll(my64[ww]);
-                                    if (e & 63) c += __popcll(my64[ew] & ((1ull << (e & 63)) - 1));
-                                    acc += neg ? (i64)c : -(i64)c;
-                                    tl += neg ? 1 : -1;
-                                    nleaves++;
+                            run = incl - run;
+                            for (u32 k = 0; k < bpl; k++) {
+                                const u32 bi = lane * bpl + k;
+                                mypre[bi] = (u16)run;
+                                run += myblk[bi];
+                            }
+                            __syncwarp();
+                        }
+                        const u64 xp = st[t].xp;
+                        auto one_leaf = [&](u32 info, u32 m32, u64 v, u32 gpf) {
+                            if (!m32 || (info >> 1) <= b || (A.trunc && gpf > A.a)) return;
+                            const bool neg = info & 1u;
+                            const u64 u = div_rcp(xp, m32, v);
+                            const u32 e = seg_count_end(u, Lw);
+                            u32 bi = e >> 8;
+                            if (bi >= nbw) bi = nbw - 1;
+                            u32 c = mypre[bi];
+                            const u32 ew = e >> 6;
+                            for (u32 ww = bi << 2; ww < ew; ww++) c += __popcll(my64[ww]);
+                            if (e & 63) c += __popcll(my64[ew] & ((1ull << (e & 63)) - 1));
+                            acc += neg ? (i64)c : -(i64)c;
+                            tl += neg ? 1 : -1;
+                            nleaves++;
+                        };
+                        one_leaf(pf_info, pf_m, pf_v, pf_gpf);                        // first 32, loaded ahead
+                        const u64 later = leafy & ~((2ull << t) - 1);
+                        if (later) prefetch(__ffsll((long long)later) - 1);           // next leaf step
+                        for (u32 base = j0 + 32; base < j1; base += 32) {             // the rest, loaded now
+                            const u32 i = base + lane;
+                            u32 info = 0, m32 = 0, gpf = 0;
+                            u64 v = 0;
+                            if (i < j1) {
+                                if (fl & 1u) {
+                                    info = ~0u;
+                                    m32 = A.primes[i];
+                                    v = A.primes_rcp[i];
+                                } else {
+                                    info = A.ml.info[i];
+                                    m32 = A.ml.m[i];
+                                    v = A.ml.rcp[i];
+                                    gpf = A.trunc ? A.ml.gpf[i] : 0;
                                 }
                             }
-                            tl = __reduce_add_sync(0xffffffffu, (u32)tl);
+                            one_leaf(info, m32, v, gpf);
                         }
+                        tl = __reduce_add_sync(0xffffffffu, (u32)tl);
                     }
                     if (lane == 0) tw[t * nw + w] = tl;
                 }
@@ -384,27 +452,27 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                                 const u32 j = lane & 7, o = lane >> 3;
                                 const u32 half = j >> 1;
                                 const u32 cword = half == 0 ? cv.x : half == 1 ? cv.y : half == 2 ? cv.z : cv.w;
-                                const u32 cj = (cword >> (16 * (j & 1))) & 0xFFFFu;
+                                const i32 cj = (i32)((cword >> (16 * (j & 1))) & 0xFFFFu);
                                 const u32 bj = ((j < 4 ? bv.x : bv.y) >> (8 * (j & 3))) & 0xFFu;
-                                for (u32 r = o;; r += 4) {
-                                    const i64 by = (i64)base + (i64)p * r + cj;
-                                    if (by >= (i64)sub_bytes) break;
-                                    if (by < 0 || (r == 0 && r8(j) < kmod)) continue;
-                                    clear_bit(((u32)by << 3) + bj);
-                                    nclears++;
-                                }
+                                // round o, or o + 4 when round 0 starts below the first cofactor;
+                                // every byte reached from there is >= 0 (k >= klo)
+                                const i32 step4 = 4 * (i32)p;
+                                i32 by = base + (i32)p * (i32)o + cj;
+                                if (o == 0 && r8(j) < kmod) by += step4;
+                                u32 n = 0;
+                                for (; by < (i32)sub_bytes; by += step4, n++) clear_bit(((u32)by << 3) + bj);
+                                nclears += n;
                             } else {
                                 // lane = whole wheel rounds, even rounds first, then odd ones
                                 for (u32 ph = 0; ph < 2; ph++) {
                                     for (u32 r = 2 * lane + ph;; r += 64) {
-                                        const i64 b0 = (i64)base + (i64)p * r;
-                                        if (b0 >= (i64)sub_bytes) break;
+                                        const i32 b0 = base + (i32)(p * r);
+                                        if (b0 >= (i32)sub_bytes) break;
 #pragma unroll
                                         for (int jj = 0; jj < 8; jj++) {
                                             if (r == 0 && r8(jj) < kmod) continue;
-                                            const i64 by = b0 + (i64)((cw4[jj >> 1] >> (16 * (jj & 1))) & 0xFFFFu);
-                                            if (by >= (i64)sub_bytes) break;
-                                            if (by < 0) continue;
+                                            const i32 by = b0 + (i32)((cw4[jj >> 1] >> (16 * (jj & 1))) & 0xFFFFu);
+                                            if (by >= (i32)sub_bytes) break;
                                             const u32 bit = ((jj < 4 ? bv.x : bv.y) >> (8 * (jj & 3))) & 0xFFu;
                                             clear_bit(((u32)by << 3) + bit);
                                             nclears++;
@@ -428,13 +496,19 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                 if (lane == 0) cw[t * nw + w] = cnt;
                 __syncwarp();
             }
+            for (u32 t = lane; t < nb; t += 32) {
+                if ((busy >> t) & 1u) continue;
+                const u64 before = busy & ((1ull << t) - 1);
+                cw[t * nw + w] = before ? cw[(63 - __clzll((long long)before)) * nw + w] : cnt0;
+            }
             __syncthreads();
             // D: segment rows, and the carries between the CTA's sub-ranges
             for (u32 t = tid; t < nb; t += NT) {
                 const u32 b = bb + t;
                 u32 C = 0;
                 for (u32 k = 0; k < nw; k++) C += cw[t * nw + k];
-                if (rep == 0 && b < Bs) A.counts[A.off[b - A.k0] + s] = C;
+                const u64 row = st[t].row;
+                if (rep == 0 && b < Bs) A.counts[row + s] = C;
                 if (b > A.kleaf) {
                     const u32* cp = t ? cw + (t - 1) * nw : prev;
                     i32 T = 0;
@@ -445,7 +519,7 @@ __global__ void __launch_bounds__(512, 2) hard_sieve_kernel(HardArgs A)
                         intra += (i64)tk * run;
                         run += cp[k];
                     }
-                    if (T) atomicAdd(&A.tallies[A.off[b - A.k0] + s], T);
+                    if (T) atomicAdd(&A.tallies[row + s], T);
                     acc += intra;
                 }
             }
@@ -579,13 +653,24 @@ __global__ void __launch_bounds__(NT) hard_combine_kernel(HardArgs A, I128Pair* 
 u32 pc_seg_bytes(pc_ctx* ctx)
 {
     u32 sb = ctx->params.seg_bytes;
-    if (sb == 0) sb = MAX_NW * MAX_SUB;
+    if (sb == 0) sb = 65536;
     if (sb < 1024) sb = 1024;
-    if (sb > MAX_NW * MAX_SUB) sb = MAX_NW * MAX_SUB;
-    if (sb > MAX_SUB) sb = sb / MAX_SUB * MAX_SUB;
+    if (sb > MAX_SEG) sb = MAX_SEG;
+    if (sb > 4096) sb = sb / 4096 * 4096;
     else if (sb > 2048) sb = 4096 > sb ? 2048 : 4096;   // sub-ranges are powers of two
     else sb = sb / 1024 * 1024;
     return sb;
+}
+
+// bytes per warp sub-range: a power of two dividing seg_bytes, at most 16 warps
+static u32 pc_sub_bytes(pc_ctx* ctx, u32 seg_bytes)
+{
+    u32 wb = ctx->params.warp_bytes ? ctx->params.warp_bytes : 8192;
+    if (wb > MAX_SUB) wb = MAX_SUB;
+    if (wb > seg_bytes) wb = seg_bytes;
+    while (seg_bytes % wb) wb >>= 1;
+    while (seg_bytes / wb > MAX_NW) wb <<= 1;
+    return wb;
 }
 
 // Work items: segments, heavy ones split into replicas; sorted by estimated
@@ -597,7 +682,7 @@ u32 pc_seg_bytes(pc_ctx* ctx)
 static void plan_items(const std::vector<u32>& segB, const std::vector<unsigned long long>& est, u32 k0, int ctas,
                        u64 x, u64 z, u64 span, std::vector<HardItem>& items)
 {
-    const double STEP_COST = 48.0, CLEAR_COST = 0.08;
+    const double STEP_COST = 128.0, CLEAR_COST = 0.08;
     const size_t nseg = segB.size();
     std::vector<double> base(nseg);
     double total = 0;
@@ -643,7 +728,7 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     if (bmax <= A.kleaf) return PC_OK;   // no hard leaf needs the sieve
     A.bmax = (u32)bmax;
     A.seg_bytes = pc_seg_bytes(ctx);
-    A.sub_bytes = A.seg_bytes < MAX_SUB ? A.seg_bytes : MAX_SUB;
+    A.sub_bytes = pc_sub_bytes(ctx, A.seg_bytes);
     A.nw = A.seg_bytes / A.sub_bytes;
     A.sub_shift = 3;
     while ((1u << A.sub_shift) < A.sub_bytes * 8) A.sub_shift++;
@@ -677,6 +762,10 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     A.off = off;
     u64 total = 0;
     PC_TRY(copy_to_host(ctx, &total, off + nrows, sizeof(u64)));
+    if (total >> 32) {
+        pc_set_error(ctx, "hard-leaf sieve: %llu count rows exceed 32-bit offsets", (unsigned long long)total);
+        return PC_EOVERFLOW;
+    }
 
     // per-segment leaf estimate, then the work items
     PC_CUDA(ctx, cudaMemsetAsync(est, 0, A.nseg * sizeof(u64), ctx->stream));
@@ -695,18 +784,25 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     const size_t smem = BATCH * sizeof(StepInfo) + A.seg_bytes + (size_t)A.nw * (A.sub_bytes >> 5) * 4 +
                         (size_t)BATCH * (A.nw + 1) * 4 + 3 * (size_t)BATCH * A.nw * 4 + (size_t)BATCH * EMAX * 4 +
                         (size_t)BATCH * A.nw;
+    cudaError_t ea = cudaFuncSetAttribute(hard_sieve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ea != cudaSuccess) {
+        pc_set_error(ctx, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(ea));
+        return PC_ECUDA;
+    }
     int per_sm = ctx->params.ctas_per_sm ? (int)ctx->params.ctas_per_sm : 0;
-    if (per_sm == 0) {
-        per_sm = (int)(ctx->smem_optin / (smem + 2048));
-        if (per_sm < 1) per_sm = 1;
-        if (per_sm > 4) per_sm = 4;
-        if (per_sm > 2 && A.nw >= 8) per_sm = 2;   // launch bounds: 2 CTAs of 512 threads
+    {
+        int fit = 0;   // resident CTAs the SM can hold (registers and shared memory)
+        PC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, hard_sieve_kernel, 32 * (int)A.nw, smem));
+        if (fit < 1) fit = 1;
+        if (per_sm == 0 || per_sm > fit) per_sm = fit > 4 ? 4 : fit;
     }
     int ctas = ctx->sm_count * per_sm;
 
     std::vector<HardItem> items;
     plan_items(hsegB, hest, A.k0, ctas, P.x, P.z, A.span, items);
     A.nitems = items.size();
+    ctx->stats.work_items = items.size();
+    for (const HardItem& it : items) ctx->stats.item_steps += hsegB[it.s] > A.k0 ? hsegB[it.s] - A.k0 : 0;
     PC_TRY(buf_reserve(ctx, ctx->counts, total * sizeof(u32)));
     PC_TRY(buf_reserve(ctx, ctx->tallies, total * sizeof(i32)));
     PC_TRY(buf_reserve(ctx, ctx->acc_seg, (size_t)ctas * sizeof(I128Pair) + items.size() * sizeof(HardItem) + 64));
@@ -724,11 +820,6 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     A.queue = ctx->queue.as<u32>();
     A.stat = (unsigned long long*)(ctx->queue.as<u32>() + 2);
 
-    cudaError_t e = cudaFuncSetAttribute(hard_sieve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) {
-        pc_set_error(ctx, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(e));
-        return PC_ECUDA;
-    }
     cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
     PC_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
     hard_sieve_kernel<<<ctas, 32 * A.nw, smem, ctx->stream>>>(A);

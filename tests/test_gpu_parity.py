@@ -55,10 +55,11 @@ def test_s2_hard_parity(ctx_small, x, alpha):
 def test_s2_hard_many_segment_sizes():
     x, y, c = 10 ** 11, 4641 * 2, 5
     want = o.leaf_sums(x, y, c)["S2_hard"]
-    for sb, cps, th in [(1024, 1, 0), (2048, 2, 0), (4096, 4, 0), (8192, 0, 0), (16384, 3, 0), (65536, 0, 0),
-                        (65536, 1, 0)]:
-        with pc.Context(0, seg_bytes=sb, ctas_per_sm=cps, threads=th) as cx:
-            assert cx.s2_hard(x, y, c) == want, (sb, cps, th)
+    for sb, cps, wb in [(1024, 1, 0), (2048, 2, 0), (4096, 4, 0), (8192, 0, 0), (16384, 3, 0), (65536, 0, 0),
+                        (65536, 1, 0), (65536, 0, 8192), (131072, 0, 8192), (131072, 0, 4096), (32768, 0, 1024),
+                        (16384, 0, 2048)]:
+        with pc.Context(0, seg_bytes=sb, ctas_per_sm=cps, warp_bytes=wb) as cx:
+            assert cx.s2_hard(x, y, c) == want, (sb, cps, wb)
 
 
 def test_truncated_phi_parts(ctx_small):
