@@ -215,6 +215,82 @@ def run_pi_mode(args):
     return 0
 
 
+def run_batch(local, n, streams, seed=0):
+    """The batched workload: n pi(x) queries, log10 x ~ U(8, 15) (seed 0),
+    as one pc_pi_count_batch call, against a host loop of plain pc_pi_count
+    calls over the same x on the same (warm) tables.  Results must agree."""
+    import paper_1503_01839_gb300 as pc
+    from paper_1503_01839_gb300 import inputs
+    xs = inputs.batch_queries(n, seed)
+    sha = hashlib.sha256(b"".join(int(v).to_bytes(8, "little") for v in xs)).hexdigest()
+    with pc.Context(local, streams=streams) as cx:
+        cx.pi_count_batch(xs)                      # builds and warms the shared tables
+        t0 = time.perf_counter()
+        got = cx.pi_count_batch(xs)
+        tb = time.perf_counter() - t0
+        launches = cx.stats()["kernel_launches"]
+        t0 = time.perf_counter()
+        plain = [cx.pi_count(v) for v in xs]
+        tl = time.perf_counter() - t0
+    assert got == plain, "batched and plain results differ"
+    return {"queries": n, "x": "floor(10^e), e ~ U(8, 15), numpy default_rng(%d)" % seed, "x_sha256": sha,
+            "slots": streams, "batch_s": tb, "batch_qps": n / tb, "plain_loop_s": tl, "plain_qps": n / tl,
+            "speedup": tl / tb, "bit_exact": True, "gpu_launches": launches}
+
+
+def run_serve(local, n, rate, streams, lo_exp=9.0, hi_exp=17.0, check=64):
+    """The served workload: a Poisson stream of pi(x) / phi(x, a) requests
+    (20 % phi, a ~ U{5..5000}, log10 x ~ U(lo_exp, hi_exp)) fed to the
+    server at their arrival times; latency = arrival to result."""
+    import random
+    import threading
+    import paper_1503_01839_gb300 as pc
+    from paper_1503_01839_gb300 import inputs
+    tr = inputs.served_trace(n, rate_per_s=rate, seed=1, lo_exp=lo_exp, hi_exp=hi_exp)
+    x_max = max(r["x"] for r in tr)
+    res = []
+    with pc.Context(local, streams=streams) as cx:
+        srv = pc.Server(cx, x_max=x_max, a_max=5000)
+        done = threading.Event()
+
+        def collect():
+            while len(res) < n:
+                res.extend(srv.poll(512, timeout_ms=50))
+            done.set()
+
+        th = threading.Thread(target=collect, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        late = 0.0
+        for i, r in enumerate(tr):
+            dt = t0 + r["t_ms"] / 1000.0 - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            else:
+                late = max(late, -dt)
+            srv.submit(pc.PC_QUERY_PHI if r["kind"] == "phi" else pc.PC_QUERY_PI, r["x"], r["a"], tag=i)
+        t_last_arrival = time.perf_counter() - t0
+        done.wait()
+        t_end = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        by = {r["tag"]: r for r in res}
+        # every result is the same as the request run alone: check a sample here (all in the tests)
+        rnd = random.Random(5)
+        for i in rnd.sample(range(n), min(check, n)):
+            q = tr[i]
+            want = cx.phi(q["x"], q["a"]) if q["kind"] == "phi" else cx.pi_count(q["x"])
+            assert by[i]["status"] == 0 and by[i]["value"] == want, (q, by[i])
+    lat = sorted(r["t_done_ms"] - r["t_submit_ms"] for r in res)
+    achieved = n / t_end
+    return {"requests": n, "offered_qps": rate, "achieved_qps": achieved, "slots": streams,
+            "x": "floor(10^e), e ~ U(%g, %g); 20%% phi(x, a), a ~ U{5..5000}; seed 1" % (lo_exp, hi_exp),
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, (99 * len(lat)) // 100)],
+            "drain_s": t_end - t_last_arrival, "feeder_max_late_ms": 1000 * late,
+            "saturated": achieved < 0.9 * rate, "max_running": st["max_running"],
+            "failed": st["failed"], "checked_alone": min(check, n)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,13 +302,23 @@ def main():
     ap.add_argument("--no-pi", action="store_true", help="skip the pi(1e16)/pi(1e18) wall-time lines")
     ap.add_argument("--x", type=float, default=1e18, help="profiling only: a smaller x than the benchmark's")
     ap.add_argument("--alpha", type=int, default=20)
-    ap.add_argument("--mode", default="s2_hard", choices=["s2_hard", "pi"],
-                    help="pi: time whole pi(x) evaluations instead (profiling aid)")
+    ap.add_argument("--mode", default="s2_hard", choices=["s2_hard", "pi", "batch", "serve"],
+                    help="pi / batch / serve: time only that part (profiling aid)")
+    ap.add_argument("--batch", type=int, default=4096, help="queries of the batched workload (0: skip)")
+    ap.add_argument("--serve", type=int, default=1000, help="requests of the served workload (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--streams", type=int, default=8, help="query slots of the batched/served forms")
     args = ap.parse_args()
     global X, ALPHA
     X, ALPHA = int(args.x), args.alpha
     if args.mode == "pi":
         return run_pi_mode(args)
+    if args.mode == "batch":
+        print(json.dumps(run_batch(0, args.batch, args.streams)), flush=True)
+        return 0
+    if args.mode == "serve":
+        print(json.dumps(run_serve(0, args.serve, args.serve_rate, args.streams)), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
 
@@ -354,6 +440,10 @@ def main():
                                 "ms": {k: round(sp[k], 3) for k in ("ms_tables", "ms_s1", "ms_trivial",
                                                                      "ms_easy", "ms_hard", "ms_p2")}}
         line["pi_wall"] = pis
+    if rank == 0 and args.batch > 0:
+        line["batch"] = run_batch(local, args.batch, args.streams)
+    if rank == 0 and args.serve > 0:
+        line["served"] = run_serve(local, args.serve, args.serve_rate, args.streams)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

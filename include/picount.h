@@ -63,7 +63,10 @@ typedef struct pc_params {
     uint32_t warp_bytes;  /* bytes of a segment each warp of the hard-leaf sieve
                              owns: 1024, 2048, 4096 or 8192, and at most 16
                              warps per segment */
-    uint32_t reserved[2];
+    uint32_t streams;     /* concurrent query slots of pc_pi_count_batch and of
+                             the server (1..64): each slot is one host thread
+                             with its own CUDA stream and scratch; default 8 */
+    uint32_t reserved;
 } pc_params;
 
 /* Counters and phase times of the last successful call. */
@@ -129,10 +132,70 @@ int pc_p2(pc_ctx* ctx, uint64_t x, uint64_t y, uint64_t* out);
  * p_a.  Requires 1 <= y <= isqrt(x) and c <= 7. */
 int pc_leaf_sums(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, uint64_t a, pc_i128 out[5]);
 
-/* pi(x_i) for n queries.  With stream == NULL, xs and out are host arrays;
- * otherwise they are device arrays and the call runs on that stream.  Tables
- * are built once for the largest query and shared by all of them. */
+/* pi(x_i) for n queries of arbitrary, mixed sizes (the batched pattern built
+ * on Sections 2-4; the paper runs one query at a time).  With stream == NULL,
+ * xs and out are host arrays; otherwise they are device arrays, read and
+ * written in order on that stream.  The tables (pi table, primes, m-list)
+ * are built once for the whole batch and shared read-only by every query;
+ * the queries, largest first, are drained by `streams` slots (pc_params),
+ * each a host thread with its own CUDA stream and scratch, so that the
+ * kernels of different queries overlap on the GPU.  Every result equals
+ * pc_pi_count(x_i, 0).  out is written only if every query succeeded;
+ * otherwise the first failure's code is returned. */
 int pc_pi_count_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint64_t* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Served queries: continuous batching over the context's tables.
+ *
+ * A server admits pi(x) and phi(x, a) requests as they arrive.  A request
+ * starts as soon as a slot is free (pc_params.streams slots) and its device
+ * scratch estimate (pc_server_footprint) fits, with those of the requests
+ * already running, in mem_budget bytes; requests start in arrival order.
+ * Requests in different slots run concurrently on the GPU, each on its own
+ * stream.  Tables for every x <= x_max and a <= a_max are built when the
+ * server is created and stay resident until it is destroyed; a request
+ * outside those bounds is rejected at submission (PC_EINVAL), one whose
+ * estimate alone exceeds the budget with PC_ENOMEM.  Results are the exact
+ * values pc_pi_count(x, 0) / pc_phi(x, a) return.  The paper has no
+ * counterpart: it is a serving layer over the method. */
+typedef struct pc_server pc_server;
+
+#define PC_QUERY_PI 0   /* value = pi(x) */
+#define PC_QUERY_PHI 1  /* value = phi(x, a) */
+
+typedef struct pc_result {
+    uint64_t tag;         /* the caller's tag from pc_server_submit */
+    uint64_t x, a;        /* the request (a = 0 for pi) */
+    uint64_t value;       /* the result, valid when status == PC_OK */
+    int32_t kind;         /* PC_QUERY_PI or PC_QUERY_PHI */
+    int32_t status;       /* PC_OK or the failure's code */
+    double t_submit_ms;   /* times since the server was created */
+    double t_start_ms;
+    double t_done_ms;
+} pc_result;
+
+typedef struct pc_server_stats {
+    uint64_t submitted, completed, failed;
+    uint64_t max_running;      /* most requests ever running at once */
+    uint64_t max_bytes;        /* largest sum of running footprints */
+    uint64_t mem_budget;
+} pc_server_stats;
+
+/* Start a server on ctx (which it uses exclusively until pc_server_destroy).
+ * mem_budget = 0 selects half of the device memory free at creation. */
+int pc_server_create(pc_ctx* ctx, uint64_t x_max, uint64_t a_max, uint64_t mem_budget, pc_server** out);
+/* Queue one request; returns at once.  kind is PC_QUERY_PI or PC_QUERY_PHI. */
+int pc_server_submit(pc_server* s, int kind, uint64_t x, uint64_t a, uint64_t tag);
+/* Move up to max finished results into out (completion order); waits up to
+ * timeout_ms (< 0: until one is ready or nothing is pending) when none is
+ * ready yet.  *n_out receives the number written. */
+int pc_server_poll(pc_server* s, pc_result* out, size_t max, int timeout_ms, size_t* n_out);
+int pc_server_get_stats(pc_server* s, pc_server_stats* out);
+/* Device scratch estimate (bytes) the server charges a request against the budget. */
+uint64_t pc_server_footprint(pc_server* s, int kind, uint64_t x, uint64_t a);
+/* Finish every queued request, stop the slots and free the server (results
+ * not yet polled are dropped).  NULL is accepted. */
+void pc_server_destroy(pc_server* s);
 
 /* ---------------------------------------------------------------------------
  * P2 for callers that cannot allocate device memory.

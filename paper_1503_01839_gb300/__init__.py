@@ -19,7 +19,11 @@ ERRORS = {-1: "PC_EINVAL", -2: "PC_ERANGE", -3: "PC_ENOMEM", -4: "PC_ECUDA", -5:
 # every symbol declared in include/picount.h
 SYMBOLS = ["pc_create", "pc_destroy", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
            "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats", "pc_strerror", "pc_last_error", "pc_version",
-           "pc_p2_noalloc"]
+           "pc_p2_noalloc", "pc_server_create", "pc_server_submit", "pc_server_poll", "pc_server_get_stats",
+           "pc_server_footprint", "pc_server_destroy"]
+
+PC_QUERY_PI = 0
+PC_QUERY_PHI = 1
 
 
 class PcI128(ctypes.Structure):
@@ -32,7 +36,7 @@ class PcI128(ctypes.Structure):
 class PcParams(ctypes.Structure):
     _fields_ = [("seg_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("threads", ctypes.c_uint32),
                 ("alpha", ctypes.c_uint32), ("c", ctypes.c_uint32), ("warp_bytes", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("streams", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class PcStats(ctypes.Structure):
@@ -44,6 +48,23 @@ class PcStats(ctypes.Structure):
                 ("ms_tables", ctypes.c_double), ("ms_s1", ctypes.c_double), ("ms_trivial", ctypes.c_double),
                 ("ms_easy", ctypes.c_double), ("ms_hard", ctypes.c_double), ("ms_p2", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_hard_sieve", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PcResult(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("x", ctypes.c_uint64), ("a", ctypes.c_uint64), ("value", ctypes.c_uint64),
+                ("kind", ctypes.c_int32), ("status", ctypes.c_int32), ("t_submit_ms", ctypes.c_double),
+                ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PcServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("max_running", ctypes.c_uint64), ("max_bytes", ctypes.c_uint64), ("mem_budget", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -81,8 +102,18 @@ def lib():
             L.pc_version.restype = ctypes.c_char_p
             L.pc_p2_noalloc.argtypes = [u64, u64, p, u64, p, p]
             L.pc_p2_noalloc.restype = ctypes.c_int
+            L.pc_server_create.argtypes = [p, u64, u64, u64, ctypes.POINTER(p)]
+            L.pc_server_submit.argtypes = [p, ctypes.c_int, u64, u64, u64]
+            L.pc_server_poll.argtypes = [p, ctypes.POINTER(PcResult), ctypes.c_size_t, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_size_t)]
+            L.pc_server_get_stats.argtypes = [p, ctypes.POINTER(PcServerStats)]
+            L.pc_server_footprint.argtypes = [p, ctypes.c_int, u64, u64]
+            L.pc_server_footprint.restype = u64
+            L.pc_server_destroy.argtypes = [p]
+            L.pc_server_destroy.restype = None
             for name in ("pc_create", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
-                         "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats"):
+                         "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats", "pc_server_create",
+                         "pc_server_submit", "pc_server_poll", "pc_server_get_stats"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -98,9 +129,9 @@ class Context:
     """One library context (device tables + scratch) on one CUDA device."""
 
     def __init__(self, device: int = 0, seg_bytes: int = 0, ctas_per_sm: int = 0, threads: int = 0,
-                 alpha: int = 0, c: int = 0, warp_bytes: int = 0):
+                 alpha: int = 0, c: int = 0, warp_bytes: int = 0, streams: int = 0):
         self._L = lib()
-        prm = PcParams(seg_bytes, ctas_per_sm, threads, alpha, c, warp_bytes)
+        prm = PcParams(seg_bytes, ctas_per_sm, threads, alpha, c, warp_bytes, streams)
         h = ctypes.c_void_p()
         rc = self._L.pc_create(ctypes.byref(h), device, ctypes.byref(prm))
         if rc != PC_OK:
@@ -175,6 +206,62 @@ class Context:
         s = PcStats()
         self._check(self._L.pc_last_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+
+class Server:
+    """Continuous-batching server over a Context (pc_server_* of picount.h):
+    submit() queues a pi(x) or phi(x, a) request and returns at once; poll()
+    returns finished results as dicts.  The context must not be used for
+    anything else while the server lives."""
+
+    def __init__(self, ctx: Context, x_max: int, a_max: int = 0, mem_budget: int = 0):
+        self._L = lib()
+        self._ctx = ctx
+        h = ctypes.c_void_p()
+        rc = self._L.pc_server_create(ctx._h, x_max, a_max, mem_budget, ctypes.byref(h))
+        if rc != PC_OK:
+            raise PicountError(rc, self._L.pc_last_error(ctx._h).decode())
+        self._h = h
+
+    def submit(self, kind: int, x: int, a: int = 0, tag: int = 0) -> None:
+        rc = self._L.pc_server_submit(self._h, kind, x, a, tag)
+        if rc != PC_OK:
+            raise PicountError(rc, "pc_server_submit rejected the request")
+
+    def poll(self, max_results: int = 256, timeout_ms: int = 0) -> list:
+        buf = (PcResult * max_results)()
+        n = ctypes.c_size_t()
+        rc = self._L.pc_server_poll(self._h, buf, max_results, timeout_ms, ctypes.byref(n))
+        if rc != PC_OK:
+            raise PicountError(rc, "pc_server_poll failed")
+        return [buf[i].as_dict() for i in range(n.value)]
+
+    def footprint(self, kind: int, x: int, a: int = 0) -> int:
+        return self._L.pc_server_footprint(self._h, kind, x, a)
+
+    def stats(self) -> dict:
+        s = PcServerStats()
+        rc = self._L.pc_server_get_stats(self._h, ctypes.byref(s))
+        if rc != PC_OK:
+            raise PicountError(rc, "pc_server_get_stats failed")
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.pc_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def p2_noalloc(x: int, y: int, primes_ptr: int, n_primes: int, out_ptr: int, stream_handle: int = 0) -> None:

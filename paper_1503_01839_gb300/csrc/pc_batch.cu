@@ -1,0 +1,456 @@
+// pc_batch.cu -- many queries at once: the batched call and the server.
+//
+// Both run queries on worker contexts.  A worker borrows the parent's tables
+// (read-only, built up front for every query it will see) and owns a CUDA
+// stream, scratch buffers and a host thread, so the kernels of different
+// queries overlap on the GPU while each query's own launches stay in order.
+// The arithmetic of a query is exactly that of pc_pi_count / pc_phi.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "pc_internal.h"
+
+static int slots_of(const pc_ctx* ctx)
+{
+    int n = (int)ctx->params.streams;
+    if (n <= 0) n = 8;
+    if (n > 64) n = 64;
+    return n;
+}
+
+// ------------------------------------------------------------- workers
+int workers_ensure(pc_ctx* ctx, int n)
+{
+    while ((int)ctx->workers.size() < n) {
+        pc_ctx* w = nullptr;
+        pc_params p = ctx->params;
+        const int rc = pc_create(&w, ctx->device, &p);
+        if (rc != PC_OK) {
+            pc_set_error(ctx, "worker context: %s", pc_strerror(rc));
+            return rc;
+        }
+        w->borrowed = true;
+        ctx->workers.push_back(w);
+    }
+    for (pc_ctx* w : ctx->workers) {
+        w->T = ctx->T;   // shallow: the parent owns every table buffer
+        w->params = ctx->params;
+        memcpy(w->tuned_alpha, ctx->tuned_alpha, sizeof(ctx->tuned_alpha));
+        memcpy(w->tuned_seg, ctx->tuned_seg, sizeof(ctx->tuned_seg));
+    }
+    return PC_OK;
+}
+
+void workers_destroy(pc_ctx* ctx)
+{
+    for (pc_ctx* w : ctx->workers) pc_destroy(w);
+    ctx->workers.clear();
+}
+
+// ------------------------------------------------------ table requirements
+// What the tables must cover for a set of queries.  This mirrors the table
+// requests of pi_count_impl, phi_impl and leaf_parts; a query that needs more
+// fails on its worker with PC_EINVAL instead of growing shared tables.
+struct TableNeeds {
+    u64 pi = 0, prime = 0, ml = 0;
+    u32 cmin = 7;
+    void add(u64 pi_, u64 prime_, u64 ml_, u32 c)
+    {
+        pi = pc_max(pi, pi_);
+        prime = pc_max(prime, prime_);
+        if (ml_) {
+            ml = pc_max(ml, ml_);
+            cmin = c < cmin ? c : cmin;
+        }
+    }
+};
+
+// primes p_1..p_n by a host sieve (n is small: the largest a of phi queries)
+static std::vector<u64> first_primes(u64 n)
+{
+    std::vector<u64> ps;
+    u64 lim = 64;
+    while (true) {
+        std::vector<char> comp(lim + 1, 0);
+        ps.clear();
+        for (u64 i = 2; i <= lim && ps.size() < n + 1; i++) {
+            if (comp[i]) continue;
+            ps.push_back(i);
+            for (u64 j = i * i; j <= lim; j += i) comp[j] = 1;
+        }
+        if (ps.size() >= n + 1) break;
+        lim *= 2;
+    }
+    return ps;   // ps[k] = p_{k+1}; n + 1 entries
+}
+
+static u32 pi_small(u64 v)   // pi(v) for v < 17
+{
+    static const u32 t[17] = {0, 0, 1, 2, 2, 3, 3, 4, 4, 4, 4, 5, 5, 6, 6, 6, 6};
+    return t[v < 17 ? v : 16];
+}
+
+static void needs_pi(const pc_ctx* ctx, u64 x, TableNeeds& N)
+{
+    if (x < 2) return;
+    if (x < (1ull << 20)) {
+        N.add(x, 64, 0, 7);
+        return;
+    }
+    const u64 r = pc_isqrt(x);
+    u64 y = (u64)choose_alpha(ctx, x) * pc_iroot3(x);
+    if (y > r) y = r;
+    if (y < 1) y = 1;
+    u32 c = ctx->params.c ? ctx->params.c : 5;
+    if (y < 17 && c > pi_small(y)) c = pi_small(y);
+    N.add(r, pc_max(y, pc_isqrt(x / y)), y, c);
+}
+
+// phi(x, a) with p_a, p_{a+1} known on the host
+static void needs_phi(const pc_ctx* ctx, u64 x, u64 a, u64 pa, u64 pa1, TableNeeds& N)
+{
+    if (a == 0 || x == 0) return;
+    const u64 r = pc_isqrt(x);
+    N.add(r, 64, 0, 7);
+    if (pa1 > r) {   // a >= pi(isqrt x): the pi(x) branch
+        needs_pi(ctx, x, N);
+        return;
+    }
+    u64 y = (u64)choose_alpha(ctx, x) * pc_iroot3(x);
+    if (y < pa) y = pa;
+    if (y > r) y = r;
+    const u32 c = a < 5 ? (u32)a : 5;
+    N.add(pc_max(r, y), pc_max(y, pc_isqrt(x / y)), y, c);
+}
+
+static int build_needs(pc_ctx* ctx, const TableNeeds& N)
+{
+    if (N.pi == 0) return PC_OK;
+    // slack for isqrt(x / y), which is not monotone in x at cube boundaries
+    const u64 prime = N.prime + N.prime / 64 + 64;
+    PC_TRY(tables_ensure(ctx, pc_max(N.pi, prime + 2048), prime, N.ml, N.cmin));
+    for (u32 c = 1; c <= 7; c++) PC_TRY(tables_phi_c(ctx, c));
+    PC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return PC_OK;
+}
+
+// ------------------------------------------------------------- run queries
+struct Query {
+    u32 kind;   // PC_QUERY_PI / PC_QUERY_PHI
+    u64 x, a;
+};
+
+static int run_one(pc_ctx* w, const Query& q, u64* out)
+{
+    memset(&w->stats, 0, sizeof(w->stats));
+    w->stats.x = q.x;
+    w->errmsg[0] = 0;
+    return q.kind == PC_QUERY_PI ? pi_count_impl(w, q.x, 0, out) : phi_impl(w, q.x, q.a, out);
+}
+
+// Runs every query on min(slots, n) workers, largest x first.
+static int run_queries(pc_ctx* ctx, const std::vector<Query>& q, std::vector<u64>& out)
+{
+    const size_t n = q.size();
+    const int W = (int)std::min<size_t>((size_t)slots_of(ctx), n);
+    PC_TRY(workers_ensure(ctx, W));
+    std::vector<size_t> order(n);
+    for (size_t i = 0; i < n; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t i, size_t j) { return q[i].x > q[j].x; });
+    std::atomic<size_t> next{0};
+    std::atomic<int> first_rc{PC_OK};
+    std::mutex mu;
+    std::vector<pc_stats> st(W);
+    auto body = [&](int k) {
+        pc_ctx* w = ctx->workers[k];
+        if (cudaSetDevice(ctx->device) != cudaSuccess) {
+            first_rc = PC_ECUDA;
+            return;
+        }
+        pc_stats acc{};
+        for (;;) {
+            const size_t i = next.fetch_add(1);
+            if (i >= n || first_rc.load() != PC_OK) break;
+            const size_t j = order[i];
+            u64 v = 0;
+            const int rc = run_one(w, q[j], &v);
+            if (rc != PC_OK) {
+                std::lock_guard<std::mutex> g(mu);
+                if (first_rc.load() == PC_OK) {
+                    first_rc = rc;
+                    pc_set_error(ctx, "query x=%llu: %s", (unsigned long long)q[j].x, w->errmsg);
+                }
+                break;
+            }
+            out[j] = v;
+            acc.kernel_launches += w->stats.kernel_launches;
+            acc.hard_leaves += w->stats.hard_leaves;
+            acc.clears += w->stats.clears;
+            acc.steps += w->stats.steps;
+            acc.segments += w->stats.segments;
+        }
+        st[k] = acc;
+    };
+    std::vector<std::thread> th;
+    for (int k = 1; k < W; k++) th.emplace_back(body, k);
+    body(0);
+    for (auto& t : th) t.join();
+    pc_stats agg{};
+    for (const pc_stats& s : st) {
+        agg.kernel_launches += s.kernel_launches;
+        agg.hard_leaves += s.hard_leaves;
+        agg.clears += s.clears;
+        agg.steps += s.steps;
+        agg.segments += s.segments;
+    }
+    ctx->stats = agg;
+    return first_rc.load();
+}
+
+extern "C" int pc_pi_count_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint64_t* out, void* stream)
+{
+    if (!ctx || (n && (!xs || !out))) return PC_EINVAL;
+    if (n == 0) return PC_OK;
+    if (ctx->borrowed) return PC_EINVAL;
+    PC_CUDA(ctx, cudaSetDevice(ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<u64> hx(n), hout(n, 0);
+    if (stream) {
+        PC_CUDA(ctx, cudaMemcpyAsync(hx.data(), xs, n * sizeof(u64), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+        PC_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+    } else {
+        memcpy(hx.data(), xs, n * sizeof(u64));
+    }
+    TableNeeds N;
+    for (size_t i = 0; i < n; i++) {
+        if (hx[i] >> 63) return PC_ERANGE;
+        needs_pi(ctx, hx[i], N);
+    }
+    PC_TRY(build_needs(ctx, N));
+    std::vector<Query> q(n);
+    for (size_t i = 0; i < n; i++) q[i] = Query{PC_QUERY_PI, hx[i], 0};
+    PC_TRY(run_queries(ctx, q, hout));
+    if (stream) {
+        PC_CUDA(ctx, cudaMemcpyAsync(out, hout.data(), n * sizeof(u64), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+        PC_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+    } else {
+        memcpy(out, hout.data(), n * sizeof(u64));
+    }
+    ctx->stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return PC_OK;
+}
+
+// ------------------------------------------------------------------ server
+struct Request {
+    pc_result r;
+    u64 foot;
+};
+
+struct pc_server {
+    pc_ctx* ctx = nullptr;
+    u64 x_max = 0, a_max = 0, budget = 0;
+    std::vector<u64> primes;   // p_1..p_{a_max+1}
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request> queue;
+    std::deque<pc_result> done;
+    std::vector<std::thread> threads;
+    u64 in_use = 0, running = 0, pending = 0;
+    bool stop = false;
+    pc_server_stats st{};
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double now_ms() const
+    {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+// pi(n) <= 1.26 n / ln n for n > 1 (Rosser and Schoenfeld 1962).  Used only
+// to size scratch estimates, never in a count.
+static double pi_upper(double n) { return n < 17 ? 7.0 : 1.26 * n / std::log(n); }
+
+// Device scratch of one query: the hard-leaf count and tally rows (at most
+// segments x pi(isqrt z) u32 pairs), per-segment and per-work-item arrays,
+// the easy-leaf ranges (one per b <= pi(y)) and the P2 segment results.
+static u64 footprint(const pc_server* s, int kind, u64 x, u64 a)
+{
+    const pc_ctx* ctx = s->ctx;
+    if (x < (1ull << 20)) return 1ull << 20;
+    const u64 r = pc_isqrt(x);
+    u64 y = (u64)choose_alpha(ctx, x) * pc_iroot3(x);
+    if (kind == PC_QUERY_PHI && a >= 1 && a <= s->a_max && s->primes[a] <= r) y = pc_max(y, s->primes[a - 1]);
+    if (y > r) y = r;
+    const u64 z = x / y;
+    u32 sb = ctx->params.seg_bytes ? ctx->params.seg_bytes : ctx->tuned_seg[decimal_digits(x)];
+    if (sb == 0) sb = 65536;
+    const double nseg = (double)(z / (30ull * sb) + 1);
+    const double B = pi_upper((double)pc_isqrt(z));
+    const double rows = nseg * B;
+    const double bytes = rows * 8.0 + nseg * 64.0 + pi_upper((double)y) * 32.0 + (double)(z / 983040 + 1) * 48.0 +
+                         (double)(4u << 20);
+    return (u64)bytes;
+}
+
+extern "C" uint64_t pc_server_footprint(pc_server* s, int kind, uint64_t x, uint64_t a)
+{
+    if (!s) return 0;
+    return footprint(s, kind, x, a);
+}
+
+static void server_slot(pc_server* s, int k)
+{
+    pc_ctx* w = s->ctx->workers[k];
+    const bool dev_ok = cudaSetDevice(s->ctx->device) == cudaSuccess;
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        // the head request starts when it fits in the budget beside the running ones
+        s->cv_work.wait(lk, [&] {
+            return (!s->queue.empty() && s->in_use + s->queue.front().foot <= s->budget) ||
+                   (s->stop && s->queue.empty());
+        });
+        if (s->queue.empty()) break;
+        Request rq = s->queue.front();
+        s->queue.pop_front();
+        s->in_use += rq.foot;
+        s->running++;
+        s->st.max_running = pc_max(s->st.max_running, s->running);
+        s->st.max_bytes = pc_max(s->st.max_bytes, s->in_use);
+        rq.r.t_start_ms = s->now_ms();
+        lk.unlock();
+        // another request may fit beside this one
+        s->cv_work.notify_one();
+        u64 v = 0;
+        const int rc = dev_ok ? run_one(w, Query{(u32)rq.r.kind, rq.r.x, rq.r.a}, &v) : PC_ECUDA;
+        lk.lock();
+        rq.r.status = rc;
+        rq.r.value = rc == PC_OK ? v : 0;
+        rq.r.t_done_ms = s->now_ms();
+        s->in_use -= rq.foot;
+        s->running--;
+        s->pending--;
+        s->st.completed++;
+        if (rc != PC_OK) s->st.failed++;
+        s->done.push_back(rq.r);
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+    }
+}
+
+extern "C" int pc_server_create(pc_ctx* ctx, uint64_t x_max, uint64_t a_max, uint64_t mem_budget, pc_server** out)
+{
+    if (!ctx || !out || ctx->borrowed) return PC_EINVAL;
+    if (x_max >> 63) return PC_ERANGE;
+    if (a_max > 100000000ull) {
+        pc_set_error(ctx, "a_max above 1e8");
+        return PC_EINVAL;
+    }
+    PC_CUDA(ctx, cudaSetDevice(ctx->device));
+    pc_server* s = new (std::nothrow) pc_server();
+    if (!s) return PC_ENOMEM;
+    s->ctx = ctx;
+    s->x_max = x_max;
+    s->a_max = a_max;
+    s->primes = first_primes(a_max + 1);
+    // the requirements grow with x inside each decade (alpha is constant there)
+    TableNeeds N;
+    std::vector<u64> reps;
+    for (u64 p = 10; p - 1 < x_max; p *= 10) {
+        reps.push_back(p - 1);
+        if (p > x_max / 10) break;
+    }
+    reps.push_back(x_max);
+    for (u64 x : reps) {
+        needs_pi(ctx, x, N);
+        if (a_max) {
+            // y is smallest for a = 1 (covered by pi(x)) and largest for a = a_max
+            needs_phi(ctx, x, a_max, s->primes[a_max - 1], s->primes[a_max], N);
+            for (u64 a = 1; a <= a_max && a <= 8; a++) needs_phi(ctx, x, a, s->primes[a - 1], s->primes[a], N);
+        }
+    }
+    int rc = build_needs(ctx, N);
+    if (rc == PC_OK) rc = workers_ensure(ctx, slots_of(ctx));
+    if (rc == PC_OK && mem_budget == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) rc = PC_ECUDA;
+        mem_budget = fr / 2;
+    }
+    if (rc != PC_OK) {
+        delete s;
+        return rc;
+    }
+    s->budget = mem_budget;
+    s->st.mem_budget = mem_budget;
+    for (int k = 0; k < slots_of(ctx); k++) s->threads.emplace_back(server_slot, s, k);
+    *out = s;
+    return PC_OK;
+}
+
+extern "C" int pc_server_submit(pc_server* s, int kind, uint64_t x, uint64_t a, uint64_t tag)
+{
+    if (!s || (kind != PC_QUERY_PI && kind != PC_QUERY_PHI)) return PC_EINVAL;
+    if (x >> 63) return PC_ERANGE;
+    if (x > s->x_max || (kind == PC_QUERY_PHI && a > s->a_max)) return PC_EINVAL;
+    Request rq{};
+    rq.r.tag = tag;
+    rq.r.kind = kind;
+    rq.r.x = x;
+    rq.r.a = kind == PC_QUERY_PHI ? a : 0;
+    rq.foot = footprint(s, kind, x, rq.r.a);
+    if (rq.foot > s->budget) return PC_ENOMEM;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (s->stop) return PC_EINVAL;
+        rq.r.t_submit_ms = s->now_ms();
+        s->queue.push_back(rq);
+        s->pending++;
+        s->st.submitted++;
+    }
+    s->cv_work.notify_one();
+    return PC_OK;
+}
+
+extern "C" int pc_server_poll(pc_server* s, pc_result* out, size_t max, int timeout_ms, size_t* n_out)
+{
+    if (!s || !n_out || (max && !out)) return PC_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto ready = [&] { return !s->done.empty() || s->pending == 0; };
+    if (timeout_ms < 0)
+        s->cv_done.wait(lk, ready);
+    else if (timeout_ms > 0)
+        s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+    size_t k = 0;
+    while (k < max && !s->done.empty()) {
+        out[k++] = s->done.front();
+        s->done.pop_front();
+    }
+    *n_out = k;
+    return PC_OK;
+}
+
+extern "C" int pc_server_get_stats(pc_server* s, pc_server_stats* out)
+{
+    if (!s || !out) return PC_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    *out = s->st;
+    return PC_OK;
+}
+
+extern "C" void pc_server_destroy(pc_server* s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto& t : s->threads) t.join();
+    delete s;
+}

@@ -76,14 +76,18 @@ extern "C" void pc_destroy(pc_ctx* ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    Tables& T = ctx->T;
-    DevBuf* bufs[] = {&T.small_primes, &T.pi_rec, &T.primes, &T.primes_rcp, &T.ml_m, &T.ml_info,
-                      &T.ml_gpf, &T.ml_rcp,
-                      &T.rank_bits, &T.rank_cnt, &ctx->seg_b, &ctx->seg_off, &ctx->counts, &ctx->tallies,
+    workers_destroy(ctx);
+    DevBuf* bufs[] = {&ctx->seg_b, &ctx->seg_off, &ctx->counts, &ctx->tallies,
                       &ctx->acc_seg, &ctx->partials, &ctx->result, &ctx->misc, &ctx->scan_tmp, &ctx->queue,
                       &ctx->easy_rng, &ctx->easy_chunk_off};
     for (DevBuf* b : bufs) buf_free(*b);
-    for (int c = 0; c < 8; c++) buf_free(T.phiT[c]);
+    if (!ctx->borrowed) {
+        Tables& T = ctx->T;
+        DevBuf* tabs[] = {&T.small_primes, &T.pi_rec, &T.primes, &T.primes_rcp, &T.ml_m, &T.ml_info,
+                          &T.ml_gpf, &T.ml_rcp, &T.rank_bits, &T.rank_cnt};
+        for (DevBuf* b : tabs) buf_free(*b);
+        for (int c = 0; c < 8; c++) buf_free(T.phiT[c]);
+    }
     if (ctx->ev_ok)
         for (int i = 0; i < 16; i++) cudaEventDestroy(ctx->ev[i]);
     if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
@@ -165,7 +169,7 @@ __global__ void nth_prime_kernel(PiTable pit, u64 a, u64 hi, u64* out)
     *out = lo;
 }
 
-static u32 default_alpha(u64 x)
+u32 default_alpha(u64 x)
 {
     // y = alpha x^(1/3): the hard-leaf sieve shrinks with alpha while the
     // easy leaves grow; values chosen from measurements on GB300
@@ -175,6 +179,29 @@ static u32 default_alpha(u64 x)
     if (d <= 12) return 2 + (d - 10);
     if (d <= 15) return 4 + 2 * (d - 12);
     return 10 + 3 * (d - 15);
+}
+
+int decimal_digits(u64 x)
+{
+    int d = 1;
+    for (u64 t = x; t >= 10; t /= 10) d++;
+    return d;
+}
+
+// alpha of a query: the context's fixed alpha, else the autotuned one for
+// x's decade, else the built-in table
+u32 choose_alpha(const pc_ctx* ctx, u64 x)
+{
+    if (ctx->params.alpha) return ctx->params.alpha;
+    const u32 t = ctx->tuned_alpha[decimal_digits(x)];
+    return t ? t : default_alpha(x);
+}
+
+// segment bytes of the hard-leaf sieve for a query (0 = built-in default)
+static u32 choose_seg(const pc_ctx* ctx, u64 x)
+{
+    if (ctx->params.seg_bytes) return 0;
+    return ctx->tuned_seg[decimal_digits(x)];
 }
 
 // Leaf decomposition of phi(x, a) and P2(x, a); a == 0 selects pi(y).
@@ -317,7 +344,7 @@ extern "C" int pc_p2(pc_ctx* ctx, uint64_t x, uint64_t y, uint64_t* out)
     return PC_OK;
 }
 
-static int pi_count_impl(pc_ctx* ctx, u64 x, u32 alpha, u64* out)
+int pi_count_impl(pc_ctx* ctx, u64 x, u32 alpha, u64* out)
 {
     if (x < 2) {
         *out = 0;
@@ -329,7 +356,8 @@ static int pi_count_impl(pc_ctx* ctx, u64 x, u32 alpha, u64* out)
         u64 v[1] = {x};
         return tables_pi_values(ctx, v, out, 1);
     }
-    if (alpha == 0) alpha = ctx->params.alpha ? ctx->params.alpha : default_alpha(x);
+    if (alpha == 0) alpha = choose_alpha(ctx, x);
+    ctx->seg_call = choose_seg(ctx, x);
     const u64 r = pc_isqrt(x);
     u64 y = (u64)alpha * pc_iroot3(x);
     if (y > r) y = r;
@@ -344,7 +372,9 @@ static int pi_count_impl(pc_ctx* ctx, u64 x, u32 alpha, u64* out)
     }
     i128 parts[5];
     u64 a = 0;
-    PC_TRY(leaf_parts(ctx, x, y, c, 0, true, parts, &a));
+    const int rc = leaf_parts(ctx, x, y, c, 0, true, parts, &a);
+    ctx->seg_call = 0;
+    if (rc != PC_OK) return rc;
     i128 pi = parts[0] + parts[1] + parts[2] + parts[3] + (i128)a - 1 - parts[4];
     if (pi < 0 || (pi >> 64) != 0) {
         pc_set_error(ctx, "pi(x) out of range: internal inconsistency");
@@ -368,12 +398,8 @@ extern "C" int pc_pi_count(pc_ctx* ctx, uint64_t x, uint32_t alpha, uint64_t* ou
     return PC_OK;
 }
 
-extern "C" int pc_phi(pc_ctx* ctx, uint64_t x, uint64_t a, uint64_t* out_phi)
+int phi_impl(pc_ctx* ctx, u64 x, u64 a, u64* out_phi)
 {
-    if (!ctx || !out_phi) return PC_EINVAL;
-    if (x >> 63) return PC_ERANGE;
-    PC_CUDA(ctx, cudaSetDevice(ctx->device));
-    stats_begin(ctx, x);
     Timer t;
     if (a == 0 || x == 0) {
         *out_phi = a == 0 ? x : 0;
@@ -398,8 +424,7 @@ extern "C" int pc_phi(pc_ctx* ctx, uint64_t x, uint64_t a, uint64_t* out_phi)
     PC_LAUNCHED(ctx);
     u64 pa = 0;
     PC_TRY(copy_to_host(ctx, &pa, ctx->misc.p, sizeof(u64)));
-    u32 alpha = ctx->params.alpha ? ctx->params.alpha : default_alpha(x);
-    u64 y = (u64)alpha * pc_iroot3(x);
+    u64 y = (u64)choose_alpha(ctx, x) * pc_iroot3(x);
     if (y < pa) y = pa;
     if (y > r) y = r;
     u32 c = a < 5 ? (u32)a : 5;
@@ -412,61 +437,14 @@ extern "C" int pc_phi(pc_ctx* ctx, uint64_t x, uint64_t a, uint64_t* out_phi)
     return PC_OK;
 }
 
-extern "C" int pc_pi_count_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint64_t* out, void* stream)
+extern "C" int pc_phi(pc_ctx* ctx, uint64_t x, uint64_t a, uint64_t* out_phi)
 {
-    if (!ctx || (n && (!xs || !out))) return PC_EINVAL;
-    if (n == 0) return PC_OK;
+    if (!ctx || !out_phi) return PC_EINVAL;
+    if (x >> 63) return PC_ERANGE;
     PC_CUDA(ctx, cudaSetDevice(ctx->device));
-    cudaStream_t saved = ctx->stream;
-    std::vector<u64> hx(n), hout(n);
-    if (stream) {
-        ctx->stream = (cudaStream_t)stream;
-        cudaError_t e = cudaMemcpyAsync(hx.data(), xs, n * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-        if (e != cudaSuccess) {
-            ctx->stream = saved;
-            pc_set_error(ctx, "batch input copy: %s", cudaGetErrorString(e));
-            return PC_ECUDA;
-        }
-    } else {
-        memcpy(hx.data(), xs, n * sizeof(u64));
-    }
-    int rc = PC_OK;
-    u64 xmax = 0;
-    for (size_t i = 0; i < n; i++) {
-        if (hx[i] >> 63) rc = PC_ERANGE;
-        if (hx[i] > xmax) xmax = hx[i];
-    }
-    pc_stats agg{};
-    if (rc == PC_OK) {
-        // one table set sized for the largest query serves the whole batch
-        const u64 r = pc_isqrt(xmax);
-        u32 alpha = ctx->params.alpha ? ctx->params.alpha : default_alpha(xmax);
-        u64 y = pc_min((u64)alpha * pc_iroot3(xmax), r);
-        rc = tables_ensure(ctx, pc_max(r, 1ull << 20), pc_max(y, pc_isqrt(xmax / pc_max(y, 1))), y, 0);
-        Timer t;
-        for (size_t i = 0; i < n && rc == PC_OK; i++) {
-            stats_begin(ctx, hx[i]);
-            rc = pi_count_impl(ctx, hx[i], 0, &hout[i]);
-            agg.kernel_launches += ctx->stats.kernel_launches;
-            agg.hard_leaves += ctx->stats.hard_leaves;
-            agg.steps += ctx->stats.steps;
-        }
-        agg.ms_total = t.ms();
-    }
-    if (rc == PC_OK) {
-        if (stream) {
-            cudaError_t e = cudaMemcpyAsync(out, hout.data(), n * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-            if (e != cudaSuccess) {
-                pc_set_error(ctx, "batch output copy: %s", cudaGetErrorString(e));
-                rc = PC_ECUDA;
-            }
-        } else {
-            memcpy(out, hout.data(), n * sizeof(u64));
-        }
-        ctx->stats = agg;
-    }
-    ctx->stream = saved;
-    return rc;
+    stats_begin(ctx, x);
+    u64 v = 0;
+    PC_TRY(phi_impl(ctx, x, a, &v));
+    *out_phi = v;
+    return PC_OK;
 }

@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(NT) hard_combine_kernel(HardArgs A, I128Pair* 
 // ---------------------------------------------------------------- host
 u32 pc_seg_bytes(pc_ctx* ctx)
 {
-    u32 sb = ctx->params.seg_bytes;
+    u32 sb = ctx->params.seg_bytes ? ctx->params.seg_bytes : ctx->seg_call;
     if (sb == 0) sb = 65536;
     if (sb < 1024) sb = 1024;
     if (sb > MAX_SEG) sb = MAX_SEG;

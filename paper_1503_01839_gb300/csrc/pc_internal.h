@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "picount.h"
@@ -92,7 +93,30 @@ struct pc_ctx {
     char errmsg[512] = {0};
     cudaEvent_t ev[16];
     bool ev_ok = false;
+    // A worker context borrows the tables of its parent (shallow copy of T):
+    // it never grows or frees them.  Batched and served queries run on
+    // workers, one host thread and one stream each, so that their kernels
+    // overlap on the device.
+    bool borrowed = false;
+    std::vector<pc_ctx*> workers;
+    // autotuned alpha and segment bytes per decimal digit count of x (0 = not tuned)
+    u32 tuned_alpha[21] = {0};
+    u32 tuned_seg[21] = {0};
+    u32 seg_call = 0;   // segment bytes chosen for the running pi(x) call (0 = default)
 };
+
+u32 default_alpha(u64 x);
+int decimal_digits(u64 x);
+u32 choose_alpha(const pc_ctx* ctx, u64 x);
+
+// Worker contexts of ctx (created on first use, tables refreshed from ctx).
+int workers_ensure(pc_ctx* ctx, int n);
+void workers_destroy(pc_ctx* ctx);
+// Build every table that queries up to x_max (pi(x) with the built-in alpha,
+// and phi(x, a) for a <= a_max) need, so that workers never grow them.
+int tables_for_queries(pc_ctx* ctx, const u64* xs, size_t n, u64 a_max);
+int pi_count_impl(pc_ctx* ctx, u64 x, u32 alpha, u64* out);
+int phi_impl(pc_ctx* ctx, u64 x, u64 a, u64* out);
 
 // ------------------------------------------------------------------- util
 // out[i] = sum_{j<i} in[j] for i < n, and out[n] = total (out has n+1 slots).

@@ -418,10 +418,18 @@ static int build_mlist(pc_ctx* ctx, u64 Y, u32 cmin)
 int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 cmin)
 {
     Tables& T = ctx->T;
-    PC_TRY(ensure_small(ctx));
     if (prime_limit < 64) prime_limit = 64;
     if (pi_limit < prime_limit + 2048) pi_limit = prime_limit + 2048;
     if (pi_limit < 65536) pi_limit = 65536;
+    if (ctx->borrowed) {
+        // a worker reads its parent's tables and must find them big enough
+        if (T.n_small && pi_limit <= T.pi_limit && prime_limit <= T.prime_limit &&
+            (ml_limit == 0 || (ml_limit <= T.ml_limit && cmin >= T.ml_cmin)))
+            return PC_OK;
+        pc_set_error(ctx, "query needs tables beyond those prepared for the batch");
+        return PC_EINVAL;
+    }
+    PC_TRY(ensure_small(ctx));
     bool new_pi = false;
     if (pi_limit > T.pi_limit) {
         // grow geometrically so that a rising sequence of queries rebuilds rarely
@@ -477,6 +485,10 @@ int tables_phi_c(pc_ctx* ctx, u32 c)
 {
     Tables& T = ctx->T;
     if (c == 0 || T.phiT_ok[c]) return PC_OK;
+    if (ctx->borrowed) {
+        pc_set_error(ctx, "phi(., %u) table was not prepared for the batch", c);
+        return PC_EINVAL;
+    }
     PC_TRY(ensure_small(ctx));
     u32 Q = 1;
     static const u32 P8[8] = {1, 2, 3, 5, 7, 11, 13, 17};

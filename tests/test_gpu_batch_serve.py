@@ -1,0 +1,136 @@
+"""GPU tests of the batched call and the server: every result equals the same
+query run alone (pc_pi_count / pc_phi) and, where the oracle is fast, the
+oracle; the server's admission respects slots and its memory budget."""
+import time
+
+import pytest
+
+import oracle as o
+import paper_1503_01839_gb300 as pc
+from paper_1503_01839_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def alone():
+    with pc.Context(0) as c:
+        yield c
+
+
+def test_batch_mixed_sizes_match_alone_and_oracle(alone):
+    xs = inputs.log_uniform_x(300, 3.0, 13.0, seed=11)
+    xs += [0, 1, 2, 3, 4, 5, 100, (1 << 20) - 1, 1 << 20, 10 ** 10, 2 ** 40, 10 ** 13]
+    with pc.Context(0, streams=8) as cx:
+        got = cx.pi_count_batch(xs)
+        st = cx.stats()
+    assert got == [alone.pi_count(x) for x in xs]
+    for x, g in zip(xs, got):
+        if x <= 10 ** 7:
+            assert g == o.pi_sieve(x), x
+    assert got[xs.index(10 ** 10)] == 455052511
+    assert st["kernel_launches"] > 0
+
+
+def test_batch_device_arrays_on_stream(alone):
+    torch = pytest.importorskip("torch")
+    xs = inputs.log_uniform_x(64, 6.0, 12.0, seed=12)
+    s = torch.cuda.Stream()
+    dx = torch.tensor(xs, dtype=torch.int64, device="cuda")
+    dout = torch.zeros(len(xs), dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    with pc.Context(0, streams=4) as cx:
+        cx.pi_count_batch((dx.data_ptr(), dout.data_ptr(), len(xs)), stream_handle=s.cuda_stream)
+    s.synchronize()
+    assert dout.cpu().tolist() == [alone.pi_count(x) for x in xs]
+
+
+def test_batch_slot_counts_agree():
+    xs = inputs.log_uniform_x(120, 8.0, 13.0, seed=13)
+    res = []
+    for streams in (1, 3, 16):
+        with pc.Context(0, streams=streams) as cx:
+            res.append(cx.pi_count_batch(xs))
+    assert res[0] == res[1] == res[2]
+
+
+def test_batch_reuses_context_and_grows_tables():
+    with pc.Context(0, streams=4) as cx:
+        small = inputs.log_uniform_x(40, 6.0, 9.0, seed=14)
+        big = inputs.log_uniform_x(40, 12.0, 14.0, seed=15)
+        a = cx.pi_count_batch(small)
+        b = cx.pi_count_batch(big)
+        a2 = cx.pi_count_batch(small)
+        assert a == a2
+        assert b == [cx.pi_count(x) for x in big]
+
+
+def test_batch_errors():
+    with pc.Context(0) as cx:
+        assert cx.pi_count_batch([]) == []
+        with pytest.raises(pc.PicountError) as e:
+            cx.pi_count_batch([10, 1 << 63])
+        assert e.value.code == -2
+        # the context stays usable
+        assert cx.pi_count_batch([10 ** 9]) == [50847534]
+
+
+def _drain(srv, n, timeout_s=600.0):
+    out = []
+    t0 = time.time()
+    while len(out) < n:
+        out += srv.poll(256, timeout_ms=200)
+        assert time.time() - t0 < timeout_s
+    return out
+
+
+def test_server_results_equal_alone(alone):
+    trace = inputs.served_trace(160, rate_per_s=4000.0, seed=21, lo_exp=6.0, hi_exp=13.0, a_hi=3000)
+    with pc.Context(0, streams=6) as cx:
+        with pc.Server(cx, x_max=10 ** 13, a_max=3000) as srv:
+            for i, r in enumerate(trace):
+                srv.submit(pc.PC_QUERY_PHI if r["kind"] == "phi" else pc.PC_QUERY_PI, r["x"], r["a"], tag=i)
+            res = _drain(srv, len(trace))
+            st = srv.stats()
+    assert st["completed"] == len(trace) and st["failed"] == 0
+    assert st["max_running"] >= 2   # requests overlapped on the device
+    by_tag = {r["tag"]: r for r in res}
+    for i, r in enumerate(trace):
+        g = by_tag[i]
+        assert g["status"] == 0
+        want = alone.phi(r["x"], r["a"]) if r["kind"] == "phi" else alone.pi_count(r["x"])
+        assert g["value"] == want, (r, g)
+        assert g["t_submit_ms"] <= g["t_start_ms"] <= g["t_done_ms"]
+    # a few against the oracle directly
+    for i, r in enumerate(trace[:40]):
+        if r["x"] <= 10 ** 8:
+            want = o.phi_brute(r["x"], r["a"]) if r["kind"] == "phi" else o.pi_sieve(r["x"])
+            assert by_tag[i]["value"] == want
+
+
+def test_server_memory_budget_admits_one_at_a_time():
+    xs = [10 ** 12 + 7919 * k for k in range(12)]
+    with pc.Context(0, streams=8) as cx:
+        with pc.Server(cx, x_max=2 * 10 ** 12, a_max=0, mem_budget=1 << 40) as probe:
+            foot = max(probe.footprint(pc.PC_QUERY_PI, x) for x in xs)
+        with pc.Server(cx, x_max=2 * 10 ** 12, a_max=0, mem_budget=foot + foot // 2) as srv:
+            for k, x in enumerate(xs):
+                srv.submit(pc.PC_QUERY_PI, x, 0, tag=k)
+            res = _drain(srv, len(xs))
+            st = srv.stats()
+            with pytest.raises(pc.PicountError) as e2:
+                srv.submit(pc.PC_QUERY_PI, 10 ** 13, 0, tag=100)   # beyond x_max
+            assert e2.value.code == -1
+        # a request whose footprint alone exceeds the budget is refused at submission
+        with pc.Server(cx, x_max=2 * 10 ** 12, a_max=0, mem_budget=foot // 2) as tiny:
+            with pytest.raises(pc.PicountError) as e3:
+                tiny.submit(pc.PC_QUERY_PI, xs[0], 0, tag=0)
+            assert e3.value.code == -3
+    assert st["max_running"] == 1
+    assert st["max_bytes"] <= foot + foot // 2
+    assert sorted(r["tag"] for r in res) == list(range(len(xs)))
+    # FIFO admission with one request at a time: starts follow submission order
+    starts = [r["t_start_ms"] for r in sorted(res, key=lambda r: r["tag"])]
+    assert starts == sorted(starts)
+    with pc.Context(0) as c1:
+        assert [r["value"] for r in sorted(res, key=lambda r: r["tag"])] == [c1.pi_count(x) for x in xs]
