@@ -116,7 +116,10 @@ __device__ __forceinline__ bool leaf_window(const HardArgs& A, u64 p, u64 vp, u6
 // segment; the CTA lists them once per batch ("events") and each warp applies
 // those in its sub-range.  Multiples of one prime are >= p integers apart, so
 // lanes never share a word there either.
-__global__ void __launch_bounds__(512, 1) hard_sieve_kernel(HardArgs A)
+// Instantiated for several (threads, resident CTAs) launch bounds: fewer
+// registers per thread buy more resident warps to hide shared-memory latency.
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // blocks of 256 bits (four 64-bit words); each lane owns bpl consecutive blocks
@@ -146,15 +149,18 @@ __global__ void __launch_bounds__(512, 1) hard_sieve_kernel(HardArgs A)
     u16* myblk = blk + w * nbw;
     u32* myblk32 = (u32*)myblk;
     u16* mypre = pre + w * nbw;
-    // count the set bits of this lane's blocks into myblk; returns the lane total
+    // count the set bits of every 256-bit block of the sub-range into myblk;
+    // returns this lane's share of the total.  Lanes read consecutive 16-byte
+    // halves of blocks (no bank conflicts) and pairs of lanes add up a block.
     auto count_blocks = [&]() -> u32 {
         u32 tot = 0;
-        for (u32 k = 0; k < bpl; k++) {
-            const u32 bi = lane * bpl + k;
-            const u32 c = __popcll(my64[4 * bi]) + __popcll(my64[4 * bi + 1]) + __popcll(my64[4 * bi + 2]) +
-                          __popcll(my64[4 * bi + 3]);
-            myblk[bi] = (u16)c;
+        const ulonglong2* h2 = (const ulonglong2*)my;
+        for (u32 k = lane; k < 2 * nbw; k += 32) {
+            const ulonglong2 v = h2[k];
+            u32 c = __popcll(v.x) + __popcll(v.y);
             tot += c;
+            c += __shfl_xor_sync(0xffffffffu, c, 1);
+            if (!(k & 1)) myblk[k >> 1] = (u16)c;
         }
         return tot;
     };
@@ -357,18 +363,37 @@ __global__ void __launch_bounds__(512, 1) hard_sieve_kernel(HardArgs A)
                         u32 j0, j1;
                         leaf_bounds(t, j0, j1);
                         {   // prefix counts of the 256-bit blocks of the sub-range
-                            u32 run = 0;
-                            for (u32 k = 0; k < bpl; k++) run += myblk[lane * bpl + k];
-                            u32 incl = run;
-                            for (int o = 1; o < 32; o <<= 1) {
-                                u32 v = __shfl_up_sync(0xffffffffu, incl, o);
-                                if (lane >= o) incl += v;
-                            }
-                            run = incl - run;
-                            for (u32 k = 0; k < bpl; k++) {
-                                const u32 bi = lane * bpl + k;
-                                mypre[bi] = (u16)run;
-                                run += myblk[bi];
+                            if (bpl == 8) {   // one 16-byte load and store per lane
+                                const uint4 q = ((const uint4*)myblk)[lane];
+                                const u32 c01 = (q.x & 0xFFFFu) + (q.x >> 16), c23 = (q.y & 0xFFFFu) + (q.y >> 16);
+                                const u32 c45 = (q.z & 0xFFFFu) + (q.z >> 16), c67 = (q.w & 0xFFFFu) + (q.w >> 16);
+                                const u32 own = c01 + c23 + c45 + c67;
+                                u32 incl = own;
+                                for (int o = 1; o < 32; o <<= 1) {
+                                    u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+                                    if (lane >= o) incl += v;
+                                }
+                                const u32 r0 = incl - own, r2 = r0 + c01, r4 = r2 + c23, r6 = r4 + c45;
+                                uint4 o4;
+                                o4.x = r0 | ((r0 + (q.x & 0xFFFFu)) << 16);
+                                o4.y = r2 | ((r2 + (q.y & 0xFFFFu)) << 16);
+                                o4.z = r4 | ((r4 + (q.z & 0xFFFFu)) << 16);
+                                o4.w = r6 | ((r6 + (q.w & 0xFFFFu)) << 16);
+                                ((uint4*)mypre)[lane] = o4;
+                            } else {
+                                u32 run = 0;
+                                for (u32 k = 0; k < bpl; k++) run += myblk[lane * bpl + k];
+                                u32 incl = run;
+                                for (int o = 1; o < 32; o <<= 1) {
+                                    u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+                                    if (lane >= o) incl += v;
+                                }
+                                run = incl - run;
+                                for (u32 k = 0; k < bpl; k++) {
+                                    const u32 bi = lane * bpl + k;
+                                    mypre[bi] = (u16)run;
+                                    run += myblk[bi];
+                                }
                             }
                             __syncwarp();
                         }
@@ -784,18 +809,45 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     const size_t smem = BATCH * sizeof(StepInfo) + A.seg_bytes + (size_t)A.nw * (A.sub_bytes >> 5) * 4 +
                         (size_t)BATCH * (A.nw + 1) * 4 + 3 * (size_t)BATCH * A.nw * 4 + (size_t)BATCH * EMAX * 4 +
                         (size_t)BATCH * A.nw;
-    cudaError_t ea = cudaFuncSetAttribute(hard_sieve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (ea != cudaSuccess) {
-        pc_set_error(ctx, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(ea));
-        return PC_ECUDA;
-    }
-    int per_sm = ctx->params.ctas_per_sm ? (int)ctx->params.ctas_per_sm : 0;
-    {
+    // the instantiation: the most resident warps (registers and shared memory
+    // permitting), or at least ctas_per_sm resident CTAs when that is set
+    struct Variant {
+        void (*fn)(HardArgs);
+        int maxt, minb;
+    };
+    static const Variant variants[] = {{hard_sieve_kernel<512, 1>, 512, 1}, {hard_sieve_kernel<256, 3>, 256, 3},
+                                       {hard_sieve_kernel<512, 2>, 512, 2}, {hard_sieve_kernel<256, 4>, 256, 4}};
+    const int nt = 32 * (int)A.nw;
+    const int want = (int)ctx->params.ctas_per_sm;
+    void (*kern)(HardArgs) = nullptr;
+    int per_sm = 0;
+    for (const Variant& v : variants) {
+        if (nt > v.maxt) continue;
+        cudaError_t ea = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ea != cudaSuccess) {
+            pc_set_error(ctx, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(ea));
+            return PC_ECUDA;
+        }
         int fit = 0;   // resident CTAs the SM can hold (registers and shared memory)
-        PC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, hard_sieve_kernel, 32 * (int)A.nw, smem));
-        if (fit < 1) fit = 1;
-        if (per_sm == 0 || per_sm > fit) per_sm = fit > 4 ? 4 : fit;
+        PC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, v.fn, nt, smem));
+        if (fit < 1) continue;
+        if (want) {
+            // the least register-constrained variant reaching the requested residency
+            if (!kern || (per_sm < want && fit > per_sm)) {
+                kern = v.fn;
+                per_sm = fit;
+            }
+        } else if (fit > per_sm) {
+            kern = v.fn;
+            per_sm = fit;
+        }
     }
+    if (!kern) {
+        pc_set_error(ctx, "hard-leaf sieve: no launch configuration fits (smem=%zu, threads=%d)", smem, nt);
+        return PC_EINVAL;
+    }
+    if (want && per_sm > want) per_sm = want;
+    if (per_sm > 4) per_sm = 4;
     int ctas = ctx->sm_count * per_sm;
 
     std::vector<HardItem> items;
@@ -822,7 +874,7 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 
     cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
     PC_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-    hard_sieve_kernel<<<ctas, 32 * A.nw, smem, ctx->stream>>>(A);
+    kern<<<ctas, nt, smem, ctx->stream>>>(A);
     PC_LAUNCHED(ctx);
     PC_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
     ctx->stats.kernel_launches++;
