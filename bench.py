@@ -291,6 +291,22 @@ def run_serve(local, n, rate, streams, lo_exp=9.0, hi_exp=17.0, check=64):
             "failed": st["failed"], "checked_alone": min(check, n)}
 
 
+def max_over_ranks(v, world):
+    """The largest of every rank's v (the slowest replica sets the job's time)."""
+    if world <= 1:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t[0])
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units, timed by the slowest one."""
+    return world * units_per_rank / seconds
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,13 +384,9 @@ def main():
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t[0])
+    tot_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = tot_ms / args.steps
-    value = world * z / (ms_per_step / 1000.0)
+    value = job_throughput(z, world, ms_per_step / 1000.0)
 
     # end to end through the C ABI: host scalars in, host int128 out
     e2e_times = []
@@ -385,11 +397,7 @@ def main():
         v = ctx.s2_hard(x, y, c)
         e2e_times.append(time.perf_counter() - t0)
         assert v == ref
-    e2e_s = statistics.mean(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t[0])
+    e2e_s = max_over_ranks(statistics.mean(e2e_times), world)
 
     st = stats[-1]
     sieve_ms = statistics.mean(s["ms_hard_sieve"] for s in stats)
@@ -410,7 +418,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": config(int(st["seg_bytes"])),
-            "e2e": {"value": world * z / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 24, "d2h_bytes_per_step": 16},
+            "e2e": {"value": job_throughput(z, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 24, "d2h_bytes_per_step": 16},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G smem-bank-accesses/s",
                          "frac": achieved / peak, "traffic": traffic,
