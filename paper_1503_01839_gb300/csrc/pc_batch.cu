@@ -290,7 +290,7 @@ static u64 footprint(const pc_server* s, int kind, u64 x, u64 a)
     if (y > r) y = r;
     const u64 z = x / y;
     u32 sb = ctx->params.seg_bytes ? ctx->params.seg_bytes : ctx->tuned_seg[decimal_digits(x)];
-    if (sb == 0) sb = 65536;
+    if (sb == 0) sb = 32768;
     const double nseg = (double)(z / (30ull * sb) + 1);
     const double B = pi_upper((double)pc_isqrt(z));
     const double rows = nseg * B;

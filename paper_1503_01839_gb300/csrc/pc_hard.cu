@@ -41,7 +41,6 @@
 #include "pc_sieve.cuh"
 
 static constexpr u32 BATCH = 64;
-static constexpr u32 EMAX = 48;        // multiples of one large prime in a segment (at most 48)
 static constexpr u32 RECOUNT_P = 128;   // below this a warp recounts its blocks after crossing off
 static constexpr u32 MAX_NW = 16;       // warps (sub-ranges) per segment
 static constexpr u32 MAX_SUB = 8192;    // bytes per sub-range: up to 256 blocks of 256 bits
@@ -86,14 +85,12 @@ struct __align__(16) StepInfo {
     u64 vp;        // floor((2^64 - 1) / p_b)
     u32 p;
     u32 r0;        // L mod p_b
-    u16 coff[8];   // floor(p * R8[j] / 30): byte offset of class j inside a wheel round
+    u32 coff[8];   // floor(p * R8[j] / 30): byte offset of class j inside a wheel round
     u8 cbit[8];    // bit of class j inside its byte
-    u32 flags;     // bit 0: leaves are primes, bit 1: step has leaves, bit 2: cross off by events
-    u32 ne;        // events (multiples of p_b in the segment), bit 2 only
+    u32 flags;     // bit 0: leaves are primes, bit 1: step has leaves
     u32 pself;     // segment bit of p_b itself, or ~0
-    u32 wmask;     // warps whose sub-range holds an event
     u32 row;       // off[b - k0]: start of the count / tally rows of b
-    u32 pad;
+    u32 pad[3];
 };
 
 // leaf range of prime b in the segment [L, L + span): m in (mlo, mhi].
@@ -133,8 +130,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
     u32* cw = I + BATCH * (nw + 1);                // BATCH * nw
     i32* tw = (i32*)(cw + BATCH * nw);             // BATCH * nw
     i32* basew = tw + BATCH * nw;                  // BATCH * nw
-    u32* ev = (u32*)(basew + BATCH * nw);          // BATCH * EMAX
-    u8* kmodw = (u8*)(ev + BATCH * EMAX);          // BATCH * nw
+    u8* kmodw = (u8*)(basew + BATCH * nw);         // BATCH * nw
 
     __shared__ u32 patw[80];
     __shared__ u32 prev[MAX_NW];
@@ -210,46 +206,16 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 si.q = div_rcp(L, p, vp);
                 si.r0 = (u32)(L - si.q * p);
                 si.row = (u32)A.off[b - A.k0];
-                si.pad = 0;
+                si.pad[0] = si.pad[1] = si.pad[2] = 0;
                 si.flags = 0;
                 si.mlo = si.mhi = 0;
-                si.ne = 0;
-                si.wmask = 0;
                 si.pself = (p >= L && p < L + A.span) ? seg_pos(p, L) : ~0u;
                 if (b > A.kleaf && b <= A.a && leaf_window(A, p, vp, si.xp, L, rLk[0], rLk[nw], si.mlo, si.mhi))
                     si.flags = 2u | (p * p > A.y ? 1u : 0u);
                 for (int j = 0; j < 8; j++) {
-                    si.coff[j] = 0;
-                    si.cbit[j] = 0;
-                }
-                if (b < Bs) {
-                    if (p * 4 >= A.seg_bytes) {
-                        si.flags |= 4u;
-                        u64 k = si.q + (si.r0 != 0);
-                        if (k < p) k = p;
-                        k = coprime30_at_or_after(k);
-                        u32 r = (u32)(k % 30);
-                        u64 n = k * p;
-                        const u64 end = L + A.span;
-                        u32 ne = 0, wm = 0;
-                        while (n < end && ne < EMAX) {
-                            const u32 pos = seg_pos(n, L);
-                            ev[t * EMAX + ne++] = pos;
-                            wm |= 1u << (pos >> A.sub_shift);
-                            const u32 d = next30(r);
-                            r += d;
-                            if (r >= 30) r -= 30;
-                            n += p * d;
-                        }
-                        si.ne = ne;
-                        si.wmask = wm;
-                    } else {
-                        for (int j = 0; j < 8; j++) {
-                            const u32 pr = (u32)p * r8(j);
-                            si.coff[j] = (u16)(pr / 30);
-                            si.cbit[j] = (u8)idx30(pr % 30);
-                        }
-                    }
+                    const u32 pr = (u32)p * r8(j);
+                    si.coff[j] = pr / 30;
+                    si.cbit[j] = (u8)idx30(pr % 30);
                 }
                 st[t] = si;
             }
@@ -276,7 +242,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
             for (u32 idx = tid; idx < nb * nw; idx += NT) {
                 const u32 t = idx / nw, k = idx - t * nw;
                 const StepInfo& si = st[t];
-                if (si.flags & 4u || bb + t >= Bs) continue;
+                if (bb + t >= Bs) continue;
                 const u64 p = si.p;
                 u64 klo = si.q + div_rcp((u64)si.r0 + k * A.dspan + p - 1, p, si.vp);   // ceil(L_k / p)
                 if (klo < p) klo = p;
@@ -309,7 +275,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 if (t < nb) {
                     const u32 b = bb + t, fl = st[t].flags, ps = st[t].pself;
                     if (b < Bs) {
-                        if (!(fl & 4u) || ((st[t].wmask >> w) & 1u)) on = true;
+                        if (basew[t * nw + w] < (i32)sub_bytes) on = true;
                         if (ps != ~0u && (ps >> A.sub_shift) == w) on = true;
                     }
                     if (b > A.kleaf && (fl & 2u)) {
@@ -451,33 +417,17 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                             if (!recount) atomicSub(&myblk32[pos >> 9], 1u << (16 * ((pos >> 8) & 1)));
                         }
                     };
-                    if (fl & 4u) {
-                        // large prime: its few multiples, listed by the CTA
-                        if ((st[t].wmask >> w) & 1u) {
-                            const u32 ne = st[t].ne;
-                            for (u32 e = lane; e < ne; e += 32) {
-                                const u32 pos = ev[t * EMAX + e];
-                                if ((pos >> A.sub_shift) == w) {
-                                    clear_bit(pos & (sub_bits - 1));
-                                    nclears++;
-                                }
-                            }
-                        }
-                    } else {
+                    {
                         const i32 base = basew[t * nw + w];
                         if (base < (i32)sub_bytes) {
                             const u32 kmod = kmodw[t * nw + w];
-                            const uint4 cv = *(const uint4*)st[t].coff;
                             const uint2 bv = *(const uint2*)st[t].cbit;
-                            const u32 cw4[4] = {cv.x, cv.y, cv.z, cv.w};
                             if (p >= 128) {
                                 // lane = (class j, round offset o): four rounds per pass.
                                 // Two crossings of one prime p >= 128 by different lanes
                                 // are >= 4 bytes apart, so no two lanes share a word.
                                 const u32 j = lane & 7, o = lane >> 3;
-                                const u32 half = j >> 1;
-                                const u32 cword = half == 0 ? cv.x : half == 1 ? cv.y : half == 2 ? cv.z : cv.w;
-                                const i32 cj = (i32)((cword >> (16 * (j & 1))) & 0xFFFFu);
+                                const i32 cj = (i32)st[t].coff[j];
                                 const u32 bj = ((j < 4 ? bv.x : bv.y) >> (8 * (j & 3))) & 0xFFu;
                                 // round o, or o + 4 when round 0 starts below the first cofactor;
                                 // every byte reached from there is >= 0 (k >= klo)
@@ -488,6 +438,8 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                                 for (; by < (i32)sub_bytes; by += step4, n++) clear_bit(((u32)by << 3) + bj);
                                 nclears += n;
                             } else {
+                                const uint4 c0 = *(const uint4*)st[t].coff, c1 = *(const uint4*)(st[t].coff + 4);
+                                const u32 cw8[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
                                 // lane = whole wheel rounds, even rounds first, then odd ones
                                 for (u32 ph = 0; ph < 2; ph++) {
                                     for (u32 r = 2 * lane + ph;; r += 64) {
@@ -496,7 +448,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
 #pragma unroll
                                         for (int jj = 0; jj < 8; jj++) {
                                             if (r == 0 && r8(jj) < kmod) continue;
-                                            const i32 by = b0 + (i32)((cw4[jj >> 1] >> (16 * (jj & 1))) & 0xFFFFu);
+                                            const i32 by = b0 + (i32)cw8[jj];
                                             if (by >= (i32)sub_bytes) break;
                                             const u32 bit = ((jj < 4 ? bv.x : bv.y) >> (8 * (jj & 3))) & 0xFFu;
                                             clear_bit(((u32)by << 3) + bit);
@@ -675,10 +627,10 @@ __global__ void __launch_bounds__(NT) hard_combine_kernel(HardArgs A, I128Pair* 
 }
 
 // ---------------------------------------------------------------- host
-u32 pc_seg_bytes(pc_ctx* ctx)
+u32 pc_seg_bytes(pc_ctx* ctx, u32 dflt)
 {
     u32 sb = ctx->params.seg_bytes ? ctx->params.seg_bytes : ctx->seg_call;
-    if (sb == 0) sb = 65536;
+    if (sb == 0) sb = dflt;
     if (sb < 1024) sb = 1024;
     if (sb > MAX_SEG) sb = MAX_SEG;
     if (sb > 4096) sb = sb / 4096 * 4096;
@@ -752,7 +704,8 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     const u64 bmax = P.B < P.a ? P.B : P.a;
     if (bmax <= A.kleaf) return PC_OK;   // no hard leaf needs the sieve
     A.bmax = (u32)bmax;
-    A.seg_bytes = pc_seg_bytes(ctx);
+    // 32 KiB segments of four 8 KiB warp sub-ranges: four CTAs fit on an SM
+    A.seg_bytes = pc_seg_bytes(ctx, 32768);
     A.sub_bytes = pc_sub_bytes(ctx, A.seg_bytes);
     A.nw = A.seg_bytes / A.sub_bytes;
     A.sub_shift = 3;
@@ -807,7 +760,7 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     (void)nbw;
     static_assert(sizeof(StepInfo) % 16 == 0, "StepInfo must keep 16-byte alignment");
     const size_t smem = BATCH * sizeof(StepInfo) + A.seg_bytes + (size_t)A.nw * (A.sub_bytes >> 5) * 4 +
-                        (size_t)BATCH * (A.nw + 1) * 4 + 3 * (size_t)BATCH * A.nw * 4 + (size_t)BATCH * EMAX * 4 +
+                        (size_t)BATCH * (A.nw + 1) * 4 + 3 * (size_t)BATCH * A.nw * 4 +
                         (size_t)BATCH * A.nw;
     // the instantiation: the most resident warps (registers and shared memory
     // permitting), or at least ctas_per_sm resident CTAs when that is set

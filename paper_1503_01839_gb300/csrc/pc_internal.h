@@ -163,4 +163,5 @@ struct SegGeom {
     size_t smem;
 };
 
-u32 pc_seg_bytes(pc_ctx* ctx);
+// segment bytes: the context's fixed size, else the tuned one of the call, else dflt
+u32 pc_seg_bytes(pc_ctx* ctx, u32 dflt);

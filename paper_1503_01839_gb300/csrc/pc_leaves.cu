@@ -144,13 +144,29 @@ int run_trivial(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 
 // ----------------------------------------------------------------- easy
 // Leaf ranges per b, then fixed-size chunks of leaves over all b.
+//
+// Clustered easy leaves: when m is a prime q and u = x/(p_b q) is well below
+// q, consecutive q share the same pi(u).  With l = pi(u), every prime q' >= q
+// with q' <= (x/p_b) / p_l has pi(x/(p_b q')) = l as well (u only falls as q'
+// grows, and stays >= p_l), so the whole run counts (run length) * (l - b + 2)
+// from one division and two pi lookups.  Those leaves (q^2 >= CLUST_K * x/p_b,
+// i.e. u <= q / CLUST_K) are walked run by run, each thread over a contiguous
+// slice; the rest one leaf per thread.
 static constexpr u32 EASY_CHUNK = 2048;
+static constexpr u32 CLUST_CHUNK = 16384;   // leaves per clustered chunk (64 per thread)
+static constexpr u64 CLUST_K = 8;
 
 struct EasyRange {
     u64 i0, i1;   // list indices [i0, i1) or prime indices (i0, i1] shifted to [i0+1, i1+1)
+    u64 im;       // first index of the clustered part (src 1), else i1
     u32 src;      // 0: m-list, 1: primes
     u32 pad;
 };
+
+__host__ __device__ inline u64 easy_chunks(const EasyRange& r)
+{
+    return (r.im - r.i0 + EASY_CHUNK - 1) / EASY_CHUNK + (r.i1 - r.im + CLUST_CHUNK - 1) / CLUST_CHUNK;
+}
 
 __global__ void easy_ranges_kernel(LeafArgs A, u64 b_lo, u64 nb, EasyRange* rng, u32* nchunk)
 {
@@ -162,21 +178,29 @@ __global__ void easy_ranges_kernel(LeafArgs A, u64 b_lo, u64 nb, EasyRange* rng,
     u64 T = pc_min(p * p, A.y);
     u64 lo = pc_max(A.y / p, xp / T);
     u64 hi = pc_min(A.y, xp / p);
-    EasyRange r{0, 0, 0, 0};
+    EasyRange r{0, 0, 0, 0, 0};
     if (hi > lo) {
         if (p * p > A.y) {
             // lpf(m) > p_b and m <= y < p_b^2: m is a prime q, p_b < q <= p_a
             u64 k0 = pc_max(pi_lookup(A.pit, lo), b);
             u64 k1 = pc_min(pi_lookup(A.pit, hi), A.a);
-            if (k1 > k0) { r.i0 = k0 + 1; r.i1 = k1 + 1; r.src = 1; }
+            if (k1 > k0) {
+                r.i0 = k0 + 1;
+                r.i1 = k1 + 1;
+                r.src = 1;
+                // clustered from the first prime q with q^2 >= CLUST_K * x/p_b
+                const u64 qc = xp > ~0ull / CLUST_K ? hi + 1 : pc_isqrt(CLUST_K * xp - 1) + 1;
+                r.im = qc > hi ? r.i1 : pc_min(pc_max(pi_lookup(A.pit, qc - 1) + 1, r.i0), r.i1);
+            }
         } else {
             r.i0 = rank_lookup(A.rk, lo);
             r.i1 = rank_lookup(A.rk, hi);
             r.src = 0;
         }
     }
+    if (r.src == 0) r.im = r.i1;
     rng[t] = r;
-    nchunk[t] = (u32)((r.i1 - r.i0 + EASY_CHUNK - 1) / EASY_CHUNK);
+    nchunk[t] = (u32)easy_chunks(r);
 }
 
 __global__ void easy_kernel(LeafArgs A, u64 b_lo, u64 nb, const EasyRange* rng, const u64* choff,
@@ -202,10 +226,34 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, u64 nb, const EasyRange* rng, 
         while (t + 1 < nb && choff[t + 1] <= ch) t++;
         u64 b = b_lo + t;
         EasyRange r = rng[t];
-        u64 start = r.i0 + (ch - choff[t]) * EASY_CHUNK;
-        u64 end = pc_min(r.i1, start + EASY_CHUNK);
+        const u64 c = ch - choff[t];
+        const u64 nsp = (r.im - r.i0 + EASY_CHUNK - 1) / EASY_CHUNK;
         u64 p = A.primes[b];
         u64 xp = div_rcp(A.x, p, A.primes_rcp[b]);
+        if (c >= nsp) {
+            // clustered chunk: each thread walks the runs of its slice of primes q
+            const u64 per = CLUST_CHUNK / blockDim.x;
+            const u64 start = r.im + (c - nsp) * CLUST_CHUNK + threadIdx.x * per;
+            const u64 end = pc_min(r.i1, start + per);
+            if (start < end) {
+                const u64 qlast = A.primes[end - 1];
+                for (u64 i = start; i < end;) {
+                    const u64 u = div_rcp(xp, A.primes[i], A.primes_rcp[i]);
+                    const u64 l = pi_lookup(A.pit, u);
+                    u64 n = 1;
+                    if (i + 1 < end) {
+                        // the run: primes q' <= (x/p_b) / p_l
+                        const u64 bound = div_rcp(xp, A.primes[l], A.primes_rcp[l]);
+                        n = bound >= qlast ? end - i : pi_lookup(A.pit, bound) - i + 1;
+                    }
+                    s += (i64)n * ((i64)l - (i64)b + 2);
+                    i += n;
+                }
+            }
+            continue;
+        }
+        const u64 start = r.i0 + c * EASY_CHUNK;
+        const u64 end = pc_min(r.im, start + EASY_CHUNK);
         for (u64 i = start + threadIdx.x; i < end; i += blockDim.x) {
             u64 m, v;
             bool neg = true;

@@ -233,7 +233,7 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     A.r = r;
     A.B = (u32)B;
     A.k0 = B >= 5 ? 5 : (u32)B;
-    A.seg_bytes = pc_seg_bytes(ctx);
+    A.seg_bytes = pc_seg_bytes(ctx, 65536);
     A.span = 30ull * A.seg_bytes;
     A.nseg = z / A.span + 1;
     A.pit = ctx->T.pi();
