@@ -144,6 +144,18 @@ int pc_leaf_sums(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, uint64_t a, pc
  * otherwise the first failure's code is returned. */
 int pc_pi_count_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint64_t* out, void* stream);
 
+/* Autotuner for pi(x) queries with alpha = 0 (the built-in choice): for every
+ * decade of x in [x_lo, x_hi], times pi(3 * 10^(d-1)) for alphas around the
+ * built-in one (alpha/2 .. 2 alpha) and hard-leaf segments of 16, 32 and
+ * 64 KiB, `reps` timed runs each (0 = 2), and keeps the fastest pair for that
+ * decade in ctx; pc_pi_count(x, 0), the batch and the server then use it.
+ * A fixed pc_params alpha or seg_bytes is kept fixed.  No result depends on
+ * the choice (every candidate's pi is compared; a mismatch is PC_EOVERFLOW).
+ * The paper tunes alpha by hand (Section 5, y_max = alpha x^(1/3)). */
+int pc_autotune(pc_ctx* ctx, uint64_t x_lo, uint64_t x_hi, uint32_t reps);
+/* The alpha and segment bytes pc_pi_count(x, 0) uses now. */
+int pc_tuned(pc_ctx* ctx, uint64_t x, uint32_t* alpha, uint32_t* seg_bytes);
+
 /* ---------------------------------------------------------------------------
  * Served queries: continuous batching over the context's tables.
  *

@@ -20,7 +20,7 @@ ERRORS = {-1: "PC_EINVAL", -2: "PC_ERANGE", -3: "PC_ENOMEM", -4: "PC_ECUDA", -5:
 SYMBOLS = ["pc_create", "pc_destroy", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
            "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats", "pc_strerror", "pc_last_error", "pc_version",
            "pc_p2_noalloc", "pc_server_create", "pc_server_submit", "pc_server_poll", "pc_server_get_stats",
-           "pc_server_footprint", "pc_server_destroy"]
+           "pc_server_footprint", "pc_server_destroy", "pc_autotune", "pc_tuned"]
 
 PC_QUERY_PI = 0
 PC_QUERY_PHI = 1
@@ -109,11 +109,13 @@ def lib():
             L.pc_server_get_stats.argtypes = [p, ctypes.POINTER(PcServerStats)]
             L.pc_server_footprint.argtypes = [p, ctypes.c_int, u64, u64]
             L.pc_server_footprint.restype = u64
+            L.pc_autotune.argtypes = [p, u64, u64, u32]
+            L.pc_tuned.argtypes = [p, u64, ctypes.POINTER(u32), ctypes.POINTER(u32)]
             L.pc_server_destroy.argtypes = [p]
             L.pc_server_destroy.restype = None
             for name in ("pc_create", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
                          "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats", "pc_server_create",
-                         "pc_server_submit", "pc_server_poll", "pc_server_get_stats"):
+                         "pc_server_submit", "pc_server_poll", "pc_server_get_stats", "pc_autotune", "pc_tuned"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -201,6 +203,14 @@ class Context:
         self._check(self._L.pc_pi_count_batch(self._h, ctypes.c_void_p(xs_ptr), n, ctypes.c_void_p(out_ptr),
                                               ctypes.c_void_p(stream_handle)))
         return None
+
+    def autotune(self, x_lo: int, x_hi: int, reps: int = 0) -> None:
+        self._check(self._L.pc_autotune(self._h, x_lo, x_hi, reps))
+
+    def tuned(self, x: int) -> tuple:
+        a, s = ctypes.c_uint32(), ctypes.c_uint32()
+        self._check(self._L.pc_tuned(self._h, x, ctypes.byref(a), ctypes.byref(s)))
+        return a.value, s.value
 
     def stats(self) -> dict:
         s = PcStats()

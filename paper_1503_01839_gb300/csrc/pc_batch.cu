@@ -454,3 +454,76 @@ extern "C" void pc_server_destroy(pc_server* s)
     for (auto& t : s->threads) t.join();
     delete s;
 }
+
+// ---------------------------------------------------------------- autotune
+// For every decade of x in [x_lo, x_hi] (x >= 2^20), time pi(x) at a
+// representative x for a few alphas around the built-in choice and a few
+// hard-leaf segment sizes, and keep the fastest pair for that decade.  Every
+// candidate must return the same pi(x); a mismatch is reported as an error.
+extern "C" int pc_autotune(pc_ctx* ctx, uint64_t x_lo, uint64_t x_hi, uint32_t reps)
+{
+    if (!ctx || ctx->borrowed || x_lo > x_hi) return PC_EINVAL;
+    if (x_hi >> 63) return PC_ERANGE;
+    PC_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (reps == 0) reps = 2;
+    const u32 fixed_alpha = ctx->params.alpha, fixed_seg = ctx->params.seg_bytes;
+    const int d0 = decimal_digits(pc_max(x_lo, 1ull << 20)), d1 = decimal_digits(x_hi);
+    for (int d = d0; d <= d1 && d <= 19; d++) {
+        // 3 * 10^(d-1): the geometric middle of the decade, inside [x_lo, x_hi]
+        u64 x = 3;
+        for (int k = 1; k < d; k++) x *= 10;
+        x = pc_min(pc_max(x, x_lo), x_hi);
+        if (x < (1ull << 20) || decimal_digits(x) != d) continue;
+        const u32 a0 = default_alpha(x);
+        u32 alphas[5] = {pc_max(1u, a0 / 2), pc_max(1u, (2 * a0) / 3), a0, (3 * a0 + 1) / 2, 2 * a0};
+        const u32 segs[3] = {16384, 32768, 65536};
+        double best_ms = 1e300;
+        u32 best_a = 0, best_s = 0;
+        u64 want = 0;
+        bool have = false;
+        ctx->tuned_alpha[d] = ctx->tuned_seg[d] = 0;
+        for (u32 ai = 0; ai < 5; ai++) {
+            if (fixed_alpha && alphas[ai] != fixed_alpha) continue;
+            if (ai && alphas[ai] == alphas[ai - 1]) continue;
+            for (u32 si = 0; si < 3; si++) {
+                if (fixed_seg && si) continue;
+                ctx->tuned_seg[d] = fixed_seg ? 0 : segs[si];
+                double ms = 1e300;
+                for (u32 r = 0; r <= reps; r++) {   // the first run builds tables and is not timed
+                    const auto t0 = std::chrono::steady_clock::now();
+                    u64 v = 0;
+                    memset(&ctx->stats, 0, sizeof(ctx->stats));
+                    PC_TRY(pi_count_impl(ctx, x, alphas[ai], &v));
+                    const double dt =
+                        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+                    if (!have) {
+                        want = v;
+                        have = true;
+                    } else if (v != want) {
+                        ctx->tuned_seg[d] = 0;
+                        pc_set_error(ctx, "autotune: pi(%llu) differs between settings", (unsigned long long)x);
+                        return PC_EOVERFLOW;
+                    }
+                    if (r && dt < ms) ms = dt;
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_a = alphas[ai];
+                    best_s = fixed_seg ? 0 : segs[si];
+                }
+            }
+        }
+        ctx->tuned_alpha[d] = fixed_alpha ? 0 : best_a;
+        ctx->tuned_seg[d] = best_s;
+    }
+    return PC_OK;
+}
+
+extern "C" int pc_tuned(pc_ctx* ctx, uint64_t x, uint32_t* alpha, uint32_t* seg_bytes)
+{
+    if (!ctx || !alpha || !seg_bytes) return PC_EINVAL;
+    const int d = decimal_digits(x);
+    *alpha = choose_alpha(ctx, x);
+    *seg_bytes = ctx->params.seg_bytes ? ctx->params.seg_bytes : (ctx->tuned_seg[d] ? ctx->tuned_seg[d] : 32768);
+    return PC_OK;
+}

@@ -247,9 +247,21 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 u64 klo = si.q + div_rcp((u64)si.r0 + k * A.dspan + p - 1, p, si.vp);   // ceil(L_k / p)
                 if (klo < p) klo = p;
                 const u64 qa = klo / 30;
-                const i64 base = (i64)(p * qa) - (i64)(L / 30 + (u64)k * sub_bytes);
+                const u32 kmod = (u32)(klo - 30 * qa);
+                i64 base = (i64)(p * qa) - (i64)(L / 30 + (u64)k * sub_bytes);
+                if (p >= 128 && base < (i64)sub_bytes) {
+                    // a large prime often has no multiple in the sub-range although a
+                    // wheel round overlaps it: look at the first multiple of every class
+                    i64 first = (i64)sub_bytes;
+#pragma unroll
+                    for (u32 j = 0; j < 8; j++) {
+                        const i64 fj = base + (i64)si.coff[j] + (r8(j) < kmod ? (i64)p : 0);
+                        first = fj < first ? fj : first;
+                    }
+                    if (first >= (i64)sub_bytes) base = sub_bytes;
+                }
                 basew[idx] = base > (i64)sub_bytes ? (i32)sub_bytes : (i32)base;
-                kmodw[idx] = (u8)(klo - 30 * qa);
+                kmodw[idx] = (u8)kmod;
             }
             __syncthreads();
             // C: every warp runs the batch over its own sub-range.  Steps that touch
@@ -371,10 +383,17 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                             const u32 e = seg_count_end(u, Lw);
                             u32 bi = e >> 8;
                             if (bi >= nbw) bi = nbw - 1;
-                            u32 c = mypre[bi];
-                            const u32 ew = e >> 6;
-                            for (u32 ww = bi << 2; ww < ew; ww++) c += __popcll(my64[ww]);
-                            if (e & 63) c += __popcll(my64[ew] & ((1ull << (e & 63)) - 1));
+                            // set bits of block bi below the end (0..256 of them): both halves
+                            // of the block at once, every word masked, no data-dependent loop
+                            const u32 rem = e - (bi << 8);
+                            const ulonglong2 h0 = ((const ulonglong2*)my64)[2 * bi];
+                            const ulonglong2 h1 = ((const ulonglong2*)my64)[2 * bi + 1];
+                            auto part = [&](u64 wv, u32 lo) -> u32 {
+                                const u32 sh = rem <= lo ? 0u : (rem - lo >= 64 ? 64u : rem - lo);
+                                const u64 mk = sh >= 64 ? ~0ull : ((1ull << sh) - 1ull);
+                                return __popcll(wv & mk);
+                            };
+                            const u32 c = mypre[bi] + part(h0.x, 0) + part(h0.y, 64) + part(h1.x, 128) + part(h1.y, 192);
                             acc += neg ? (i64)c : -(i64)c;
                             tl += neg ? 1 : -1;
                             nleaves++;

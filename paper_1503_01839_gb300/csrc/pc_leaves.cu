@@ -153,8 +153,8 @@ int run_trivial(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 // i.e. u <= q / CLUST_K) are walked run by run, each thread over a contiguous
 // slice; the rest one leaf per thread.
 static constexpr u32 EASY_CHUNK = 2048;
-static constexpr u32 CLUST_CHUNK = 16384;   // leaves per clustered chunk (64 per thread)
-static constexpr u64 CLUST_K = 8;
+static constexpr u32 CLUST_CHUNK = 65536;   // leaves per clustered chunk (256 per thread)
+static constexpr u64 CLUST_K = 2;
 
 struct EasyRange {
     u64 i0, i1;   // list indices [i0, i1) or prime indices (i0, i1] shifted to [i0+1, i1+1)

@@ -134,3 +134,20 @@ def test_server_memory_budget_admits_one_at_a_time():
     assert starts == sorted(starts)
     with pc.Context(0) as c1:
         assert [r["value"] for r in sorted(res, key=lambda r: r["tag"])] == [c1.pi_count(x) for x in xs]
+
+
+def test_autotune_keeps_results(alone):
+    with pc.Context(0, streams=4) as cx:
+        before = {x: cx.tuned(x) for x in (10 ** 9, 3 * 10 ** 10, 10 ** 12)}
+        cx.autotune(10 ** 9, 2 * 10 ** 12, reps=1)
+        after = {x: cx.tuned(x) for x in before}
+        for x, (al, sb) in after.items():
+            assert al >= 1 and sb in (16384, 32768, 65536)
+        xs = inputs.log_uniform_x(60, 9.0, 12.3, seed=31) + [10 ** 10, 10 ** 12]
+        got = cx.pi_count_batch(xs)
+        assert got == [alone.pi_count(x) for x in xs]
+        assert cx.pi_count(10 ** 10) == 455052511 and cx.pi_count(10 ** 12) == 37607912018
+    # a fixed alpha stays fixed
+    with pc.Context(0, alpha=3) as cx:
+        cx.autotune(10 ** 9, 10 ** 10, reps=1)
+        assert cx.tuned(5 * 10 ** 9)[0] == 3
