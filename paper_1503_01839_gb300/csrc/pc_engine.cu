@@ -171,14 +171,16 @@ __global__ void nth_prime_kernel(PiTable pit, u64 a, u64 hi, u64* out)
 
 u32 default_alpha(u64 x)
 {
-    // y = alpha x^(1/3): the hard-leaf sieve shrinks with alpha while the
-    // easy leaves grow; values chosen from measurements on GB300
+    // y = alpha x^(1/3): the hard-leaf sieve and P2 shrink with alpha while the
+    // easy leaves grow; values from sweeps of pi(10^n) on GB300
     int d = 0;
     for (u64 t = x; t >= 10; t /= 10) d++;
-    if (d <= 9) return 1;
-    if (d <= 12) return 2 + (d - 10);
-    if (d <= 15) return 4 + 2 * (d - 12);
-    return 10 + 3 * (d - 15);
+    if (d <= 8) return 2;
+    if (d == 9) return 4;
+    if (d <= 11) return 6;
+    if (d <= 13) return 12;
+    if (d <= 17) return 24;
+    return 40;
 }
 
 int decimal_digits(u64 x)

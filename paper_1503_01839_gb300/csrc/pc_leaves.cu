@@ -204,26 +204,30 @@ __global__ void easy_ranges_kernel(LeafArgs A, u64 b_lo, u64 nb, EasyRange* rng,
 }
 
 __global__ void easy_kernel(LeafArgs A, u64 b_lo, u64 nb, const EasyRange* rng, const u64* choff,
-                            u64 nchunks, I128Pair* part)
+                            u64 nchunks, unsigned long long* queue, I128Pair* part)
 {
     __shared__ i128 scratch[32];
-    __shared__ u64 s_b;
+    __shared__ u64 s_ch, s_t;
     i64 s = 0;
-    // a contiguous run of chunks per CTA: one search, then a linear walk over b
-    const u64 per = (nchunks + gridDim.x - 1) / gridDim.x;
-    const u64 ch0 = (u64)blockIdx.x * per, ch1 = pc_min(nchunks, ch0 + per);
-    if (threadIdx.x == 0 && ch0 < ch1) {
-        u64 lo = 0, hi = nb;   // largest t with choff[t] <= ch0
-        while (hi - lo > 1) {
-            u64 mid = (lo + hi) >> 1;
-            if (choff[mid] <= ch0) lo = mid; else hi = mid;
+    // chunks are handed out one at a time (their costs differ widely)
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const u64 ch = atomicAdd(queue, 1ull);
+            s_ch = ch;
+            if (ch < nchunks) {
+                u64 lo = 0, hi = nb;   // largest t with choff[t] <= ch
+                while (hi - lo > 1) {
+                    const u64 mid = (lo + hi) >> 1;
+                    if (choff[mid] <= ch) lo = mid; else hi = mid;
+                }
+                s_t = lo;
+            }
         }
-        s_b = lo;
-    }
-    __syncthreads();
-    u64 t = s_b;
-    for (u64 ch = ch0; ch < ch1; ch++) {
-        while (t + 1 < nb && choff[t + 1] <= ch) t++;
+        __syncthreads();
+        const u64 ch = s_ch;
+        if (ch >= nchunks) break;
+        const u64 t = s_t;
         u64 b = b_lo + t;
         EasyRange r = rng[t];
         const u64 c = ch - choff[t];
@@ -303,10 +307,12 @@ int run_easy(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     u64 nchunks = 0;
     PC_TRY(copy_to_host(ctx, &nchunks, choff + nb, sizeof(u64)));
     if (nchunks == 0) return PC_OK;
-    int g = ctx->sm_count * 8;
+    int g = (int)pc_min((u64)ctx->sm_count * 8, nchunks);
     PC_TRY(buf_reserve(ctx, ctx->partials, g * sizeof(I128Pair)));
+    PC_TRY(buf_reserve(ctx, ctx->queue, 64));
+    PC_CUDA(ctx, cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream));
     easy_kernel<<<g, 256, 0, ctx->stream>>>(A, b_lo, nb, ctx->easy_rng.as<EasyRange>(), choff, nchunks,
-                                            ctx->partials.as<I128Pair>());
+                                            (unsigned long long*)ctx->queue.p, ctx->partials.as<I128Pair>());
     PC_LAUNCHED(ctx);
     ctx->stats.kernel_launches++;
     return reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out);

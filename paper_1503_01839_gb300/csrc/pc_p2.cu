@@ -15,6 +15,7 @@
 struct P2Args {
     u64 x, y, z, r;   // r = isqrt(x)
     u32 B, k0;
+    u32 b_mid, b_big;   // first prime index >= P2_COOP_P, and with 8 p > seg_bytes
     u64 nseg;
     u32 seg_bytes;
     u64 span;
@@ -26,6 +27,12 @@ struct P2Args {
     I128Pair* acc;    // sum of local counts per segment
     u32* queue;
 };
+
+// Primes below P2_COOP_P have many wheel rounds per segment and are crossed
+// off by the whole CTA at once; the medium ones by one thread per (prime,
+// residue class); those with fewer than one round per 8 bytes by one thread
+// per prime.
+static constexpr u32 P2_COOP_P = 512;
 
 template <int NT>
 __global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A)
@@ -56,15 +63,20 @@ __global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A)
         const u64 end = L + A.span;
         // cross off p_b, k0 < b <= B (the prime itself included)
         auto none = [](u32) {};
-        u32 b = A.k0 + 1;
-        for (; b <= A.B; b++) {
+        for (u32 b = A.k0 + 1; b < A.b_mid; b++) {
             const u64 p = A.primes[b];
-            if (p * 8 > A.seg_bytes) break;
             u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[b]) : 0;
             if (ks < p) ks = p;
             cross_off_coop(bits, A.seg_bytes, L, (u32)p, ks, tid, NT, none);
         }
-        for (u32 bb = b + tid; bb <= A.B; bb += NT) {
+        for (u32 task = tid; task < 8 * (A.b_big - A.b_mid); task += NT) {
+            const u32 bb = A.b_mid + (task >> 3);
+            const u64 p = A.primes[bb];
+            u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[bb]) : 0;
+            if (ks < p) ks = p;
+            cross_off_class(bits, A.seg_bytes, L, (u32)p, ks, task & 7, none);
+        }
+        for (u32 bb = A.b_big + tid; bb <= A.B; bb += NT) {
             const u64 p = A.primes[bb];
             u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[bb]) : 0;
             if (ks < p) ks = p;
@@ -80,10 +92,9 @@ __global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A)
             }
         }
         __syncthreads();
-        for (u32 k = tid; k < nblk; k += NT) {
-            u32 c = 0;
-            for (u32 w = 0; w < 32; w++) c += __popc(bits[32 * k + w]);
-            blk[k] = c;
+        for (u32 k = wid; k < nblk; k += NT / 32) {   // a warp per 1024-bit block: no bank conflicts
+            const u32 c = __reduce_add_sync(0xffffffffu, (u32)__popc(bits[32 * k + lane]));
+            if (lane == 0) blk[k] = c;
         }
         __syncthreads();
         // exclusive scan of the block counts
@@ -235,6 +246,12 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     A.k0 = B >= 5 ? 5 : (u32)B;
     A.seg_bytes = pc_seg_bytes(ctx, 65536);
     A.span = 30ull * A.seg_bytes;
+    {
+        u64 v2[2] = {P2_COOP_P - 1, A.seg_bytes / 8}, pv2[2];
+        PC_TRY(tables_pi_values(ctx, v2, pv2, 2));
+        A.b_mid = (u32)pc_min(pc_max(pv2[0] + 1, (u64)A.k0 + 1), B + 1);
+        A.b_big = (u32)pc_min(pc_max(pv2[1] + 1, (u64)A.b_mid), B + 1);
+    }
     A.nseg = z / A.span + 1;
     A.pit = ctx->T.pi();
     A.primes = ctx->T.primes.as<u32>();

@@ -52,6 +52,28 @@ __device__ __forceinline__ u32 cross_off_coop(u32* bits, u32 seg_bytes, u64 L, u
     return n;   // multiples crossed off by this thread
 }
 
+// One thread crosses off the multiples k*p of one residue class,
+// k = 30 q + R8[j] >= kstart: one per wheel round, p bytes apart.
+template <class F>
+__device__ __forceinline__ void cross_off_class(u32* bits, u32 seg_bytes, u64 L, u32 p, u64 kstart, u32 j,
+                                                F&& newly)
+{
+    const u32 rj = r8(j);
+    u64 q = kstart / 30;
+    if (30 * q + rj < kstart) q++;
+    const u32 pr = p * rj;                 // p < 2^27 here, so no overflow
+    const u32 bit = idx30(pr % 30);
+    const u64 byte64 = (u64)p * q + pr / 30;
+    const u64 Lb = L / 30;
+    if (byte64 < Lb) return;               // cannot happen for kstart*p >= L
+    for (u64 by = byte64 - Lb; by < seg_bytes; by += p) {
+        const u32 pos = ((u32)by << 3) + bit;
+        const u32 mask = 1u << (pos & 31);
+        const u32 old = atomicAnd(&bits[pos >> 5], ~mask);
+        if (old & mask) newly(pos);
+    }
+}
+
 // One thread crosses off all multiples k*p (k >= kstart, k coprime to 30)
 // of a large prime by walking k along the wheel.
 template <class F>
