@@ -79,7 +79,7 @@ extern "C" void pc_destroy(pc_ctx* ctx)
     workers_destroy(ctx);
     DevBuf* bufs[] = {&ctx->seg_b, &ctx->seg_off, &ctx->counts, &ctx->tallies,
                       &ctx->acc_seg, &ctx->partials, &ctx->result, &ctx->misc, &ctx->scan_tmp, &ctx->queue,
-                      &ctx->easy_rng, &ctx->easy_chunk_off};
+                      &ctx->easy_rng, &ctx->easy_chunk_off, &ctx->easy_cmap};
     for (DevBuf* b : bufs) buf_free(*b);
     if (!ctx->borrowed) {
         Tables& T = ctx->T;

@@ -86,7 +86,7 @@ struct pc_ctx {
     Tables T;
     // scratch (grow-only)
     DevBuf seg_b, seg_off, counts, tallies, acc_seg, partials, result, misc, scan_tmp, queue;
-    DevBuf easy_rng, easy_chunk_off;
+    DevBuf easy_rng, easy_chunk_off, easy_cmap;
     // pinned host staging for small results
     void* host_stage = nullptr;
     pc_stats stats{};

@@ -152,7 +152,7 @@ int run_trivial(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 // from one division and two pi lookups.  Those leaves (q^2 >= CLUST_K * x/p_b,
 // i.e. u <= q / CLUST_K) are walked run by run, each thread over a contiguous
 // slice; the rest one leaf per thread.
-static constexpr u32 EASY_CHUNK = 2048;
+static constexpr u32 EASY_CHUNK = 8192;
 static constexpr u32 CLUST_CHUNK = 65536;   // leaves per clustered chunk (256 per thread)
 static constexpr u64 CLUST_K = 2;
 
@@ -203,31 +203,28 @@ __global__ void easy_ranges_kernel(LeafArgs A, u64 b_lo, u64 nb, EasyRange* rng,
     nchunk[t] = (u32)easy_chunks(r);
 }
 
-__global__ void easy_kernel(LeafArgs A, u64 b_lo, u64 nb, const EasyRange* rng, const u64* choff,
+// chunk -> index t = b - b_lo of the prime whose leaves it holds
+__global__ void easy_chunk_map_kernel(u64 nb, const u64* choff, u32* cmap)
+{
+    const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    for (u64 ch = choff[t]; ch < choff[t + 1]; ch++) cmap[ch] = (u32)t;
+}
+
+__global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u64* choff, const u32* cmap,
                             u64 nchunks, unsigned long long* queue, I128Pair* part)
 {
     __shared__ i128 scratch[32];
-    __shared__ u64 s_ch, s_t;
+    __shared__ u64 s_ch;
     i64 s = 0;
     // chunks are handed out one at a time (their costs differ widely)
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) {
-            const u64 ch = atomicAdd(queue, 1ull);
-            s_ch = ch;
-            if (ch < nchunks) {
-                u64 lo = 0, hi = nb;   // largest t with choff[t] <= ch
-                while (hi - lo > 1) {
-                    const u64 mid = (lo + hi) >> 1;
-                    if (choff[mid] <= ch) lo = mid; else hi = mid;
-                }
-                s_t = lo;
-            }
-        }
+        if (threadIdx.x == 0) s_ch = atomicAdd(queue, 1ull);
         __syncthreads();
         const u64 ch = s_ch;
         if (ch >= nchunks) break;
-        const u64 t = s_t;
+        const u64 t = cmap[ch];
         u64 b = b_lo + t;
         EasyRange r = rng[t];
         const u64 c = ch - choff[t];
@@ -307,11 +304,20 @@ int run_easy(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     u64 nchunks = 0;
     PC_TRY(copy_to_host(ctx, &nchunks, choff + nb, sizeof(u64)));
     if (nchunks == 0) return PC_OK;
+    if (nchunks >> 32) {
+        pc_set_error(ctx, "easy leaves: %llu chunks", (unsigned long long)nchunks);
+        return PC_EOVERFLOW;
+    }
+    PC_TRY(buf_reserve(ctx, ctx->easy_cmap, nchunks * sizeof(u32)));
+    easy_chunk_map_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>(nb, choff,
+                                                                                 ctx->easy_cmap.as<u32>());
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
     int g = (int)pc_min((u64)ctx->sm_count * 8, nchunks);
     PC_TRY(buf_reserve(ctx, ctx->partials, g * sizeof(I128Pair)));
     PC_TRY(buf_reserve(ctx, ctx->queue, 64));
     PC_CUDA(ctx, cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream));
-    easy_kernel<<<g, 256, 0, ctx->stream>>>(A, b_lo, nb, ctx->easy_rng.as<EasyRange>(), choff, nchunks,
+    easy_kernel<<<g, 256, 0, ctx->stream>>>(A, b_lo, ctx->easy_rng.as<EasyRange>(), choff, ctx->easy_cmap.as<u32>(), nchunks,
                                             (unsigned long long*)ctx->queue.p, ctx->partials.as<I128Pair>());
     PC_LAUNCHED(ctx);
     ctx->stats.kernel_launches++;
