@@ -152,7 +152,7 @@ int run_trivial(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 // from one division and two pi lookups.  Those leaves (q^2 >= CLUST_K * x/p_b,
 // i.e. u <= q / CLUST_K) are walked run by run, each thread over a contiguous
 // slice; the rest one leaf per thread.
-static constexpr u32 EASY_CHUNK = 8192;
+static constexpr u32 EASY_CHUNK = 16384;
 static constexpr u32 CLUST_CHUNK = 65536;   // leaves per clustered chunk (256 per thread)
 static constexpr u64 CLUST_K = 2;
 
