@@ -243,7 +243,7 @@ def run_batch(local, n, streams, seed=0):
             "autotune_s": t_tune, "tuned_alpha_seg_per_decade": tuned}
 
 
-def run_serve(local, n, rate, streams, lo_exp=9.0, hi_exp=17.0, check=64):
+def run_serve(local, n, rate, streams, lo_exp=9.0, hi_exp=17.0, check=64, policy=0):
     """The served workload: a Poisson stream of pi(x) / phi(x, a) requests
     (20 % phi, a ~ U{5..5000}, log10 x ~ U(lo_exp, hi_exp)) fed to the
     server at their arrival times; latency = arrival to result."""
@@ -255,7 +255,7 @@ def run_serve(local, n, rate, streams, lo_exp=9.0, hi_exp=17.0, check=64):
     x_max = max(r["x"] for r in tr)
     res = []
     with pc.Context(local, streams=streams) as cx:
-        srv = pc.Server(cx, x_max=x_max, a_max=5000)
+        srv = pc.Server(cx, x_max=x_max, a_max=5000, policy=policy)
         done = threading.Event()
 
         def collect():
@@ -288,7 +288,8 @@ def run_serve(local, n, rate, streams, lo_exp=9.0, hi_exp=17.0, check=64):
             assert by[i]["status"] == 0 and by[i]["value"] == want, (q, by[i])
     lat = sorted(r["t_done_ms"] - r["t_submit_ms"] for r in res)
     achieved = n / t_end
-    return {"requests": n, "offered_qps": rate, "achieved_qps": achieved, "slots": streams,
+    return {"policy": ["fifo", "small_first"][policy], "requests": n, "offered_qps": rate,
+            "achieved_qps": achieved, "slots": streams,
             "x": "floor(10^e), e ~ U(%g, %g); 20%% phi(x, a), a ~ U{5..5000}; seed 1" % (lo_exp, hi_exp),
             "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, (99 * len(lat)) // 100)],
             "drain_s": t_end - t_last_arrival, "feeder_max_late_ms": 1000 * late,
@@ -338,7 +339,8 @@ def main():
         print(json.dumps(run_batch(0, args.batch, args.streams)), flush=True)
         return 0
     if args.mode == "serve":
-        print(json.dumps(run_serve(0, args.serve, args.serve_rate, args.streams)), flush=True)
+        for pol in (0, 1):
+            print(json.dumps(run_serve(0, args.serve, args.serve_rate, args.streams, policy=pol)), flush=True)
         return 0
     if args.impl == "reference":
         return run_reference(args)
@@ -459,7 +461,7 @@ def main():
     if rank == 0 and args.batch > 0:
         line["batch"] = run_batch(local, args.batch, args.streams)
     if rank == 0 and args.serve > 0:
-        line["served"] = run_serve(local, args.serve, args.serve_rate, args.streams)
+        line["served"] = [run_serve(local, args.serve, args.serve_rate, args.streams, policy=pol) for pol in (0, 1)]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -85,6 +85,8 @@ typedef struct pc_stats {
     uint64_t kernel_launches;
     double ms_tables, ms_s1, ms_trivial, ms_easy, ms_hard, ms_p2, ms_total;
     double ms_hard_sieve;   /* the segmented sieve kernel alone (CUDA events) */
+    uint64_t warp_steps;      /* (warp sub-range, prime) steps with work in the hard-leaf sieve */
+    uint64_t leaf_warp_steps; /* of which resolved leaves */
 } pc_stats;
 
 typedef struct pc_ctx pc_ctx;
@@ -162,7 +164,11 @@ int pc_tuned(pc_ctx* ctx, uint64_t x, uint32_t* alpha, uint32_t* seg_bytes);
  * A server admits pi(x) and phi(x, a) requests as they arrive.  A request
  * starts as soon as a slot is free (pc_params.streams slots) and its device
  * scratch estimate (pc_server_footprint) fits, with those of the requests
- * already running, in mem_budget bytes; requests start in arrival order.
+ * already running, in mem_budget bytes.  The waiting requests form one queue:
+ * in arrival order (PC_SERVE_FIFO), or by x, smallest first, arrival order
+ * among equal x (PC_SERVE_SMALL_FIRST: lower median latency under overload;
+ * a large request waits while smaller ones keep arriving).  Only the head of
+ * the queue may start.
  * Requests in different slots run concurrently on the GPU, each on its own
  * stream.  Tables for every x <= x_max and a <= a_max are built when the
  * server is created and stay resident until it is destroyed; a request
@@ -171,6 +177,9 @@ int pc_tuned(pc_ctx* ctx, uint64_t x, uint32_t* alpha, uint32_t* seg_bytes);
  * values pc_pi_count(x, 0) / pc_phi(x, a) return.  The paper has no
  * counterpart: it is a serving layer over the method. */
 typedef struct pc_server pc_server;
+
+#define PC_SERVE_FIFO 0
+#define PC_SERVE_SMALL_FIRST 1
 
 #define PC_QUERY_PI 0   /* value = pi(x) */
 #define PC_QUERY_PHI 1  /* value = phi(x, a) */
@@ -195,7 +204,8 @@ typedef struct pc_server_stats {
 
 /* Start a server on ctx (which it uses exclusively until pc_server_destroy).
  * mem_budget = 0 selects half of the device memory free at creation. */
-int pc_server_create(pc_ctx* ctx, uint64_t x_max, uint64_t a_max, uint64_t mem_budget, pc_server** out);
+int pc_server_create(pc_ctx* ctx, uint64_t x_max, uint64_t a_max, uint64_t mem_budget, uint32_t policy,
+                     pc_server** out);
 /* Queue one request; returns at once.  kind is PC_QUERY_PI or PC_QUERY_PHI. */
 int pc_server_submit(pc_server* s, int kind, uint64_t x, uint64_t a, uint64_t tag);
 /* Move up to max finished results into out (completion order); waits up to

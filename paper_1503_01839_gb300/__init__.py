@@ -24,6 +24,8 @@ SYMBOLS = ["pc_create", "pc_destroy", "pc_set_stream", "pc_pi_count", "pc_phi", 
 
 PC_QUERY_PI = 0
 PC_QUERY_PHI = 1
+PC_SERVE_FIFO = 0
+PC_SERVE_SMALL_FIRST = 1
 
 
 class PcI128(ctypes.Structure):
@@ -47,7 +49,8 @@ class PcStats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64),
                 ("ms_tables", ctypes.c_double), ("ms_s1", ctypes.c_double), ("ms_trivial", ctypes.c_double),
                 ("ms_easy", ctypes.c_double), ("ms_hard", ctypes.c_double), ("ms_p2", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("ms_hard_sieve", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("ms_hard_sieve", ctypes.c_double),
+                ("warp_steps", ctypes.c_uint64), ("leaf_warp_steps", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -102,7 +105,7 @@ def lib():
             L.pc_version.restype = ctypes.c_char_p
             L.pc_p2_noalloc.argtypes = [u64, u64, p, u64, p, p]
             L.pc_p2_noalloc.restype = ctypes.c_int
-            L.pc_server_create.argtypes = [p, u64, u64, u64, ctypes.POINTER(p)]
+            L.pc_server_create.argtypes = [p, u64, u64, u64, u32, ctypes.POINTER(p)]
             L.pc_server_submit.argtypes = [p, ctypes.c_int, u64, u64, u64]
             L.pc_server_poll.argtypes = [p, ctypes.POINTER(PcResult), ctypes.c_size_t, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_size_t)]
@@ -224,11 +227,11 @@ class Server:
     returns finished results as dicts.  The context must not be used for
     anything else while the server lives."""
 
-    def __init__(self, ctx: Context, x_max: int, a_max: int = 0, mem_budget: int = 0):
+    def __init__(self, ctx: Context, x_max: int, a_max: int = 0, mem_budget: int = 0, policy: int = PC_SERVE_FIFO):
         self._L = lib()
         self._ctx = ctx
         h = ctypes.c_void_p()
-        rc = self._L.pc_server_create(ctx._h, x_max, a_max, mem_budget, ctypes.byref(h))
+        rc = self._L.pc_server_create(ctx._h, x_max, a_max, mem_budget, policy, ctypes.byref(h))
         if rc != PC_OK:
             raise PicountError(rc, self._L.pc_last_error(ctx._h).decode())
         self._h = h

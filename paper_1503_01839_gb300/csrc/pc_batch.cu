@@ -257,6 +257,7 @@ struct Request {
 struct pc_server {
     pc_ctx* ctx = nullptr;
     u64 x_max = 0, a_max = 0, budget = 0;
+    u32 policy = PC_SERVE_FIFO;
     std::vector<u64> primes;   // p_1..p_{a_max+1}
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -344,9 +345,10 @@ static void server_slot(pc_server* s, int k)
     }
 }
 
-extern "C" int pc_server_create(pc_ctx* ctx, uint64_t x_max, uint64_t a_max, uint64_t mem_budget, pc_server** out)
+extern "C" int pc_server_create(pc_ctx* ctx, uint64_t x_max, uint64_t a_max, uint64_t mem_budget, uint32_t policy,
+                                pc_server** out)
 {
-    if (!ctx || !out || ctx->borrowed) return PC_EINVAL;
+    if (!ctx || !out || ctx->borrowed || policy > PC_SERVE_SMALL_FIRST) return PC_EINVAL;
     if (x_max >> 63) return PC_ERANGE;
     if (a_max > 100000000ull) {
         pc_set_error(ctx, "a_max above 1e8");
@@ -356,6 +358,7 @@ extern "C" int pc_server_create(pc_ctx* ctx, uint64_t x_max, uint64_t a_max, uin
     pc_server* s = new (std::nothrow) pc_server();
     if (!s) return PC_ENOMEM;
     s->ctx = ctx;
+    s->policy = policy;
     s->x_max = x_max;
     s->a_max = a_max;
     s->primes = first_primes(a_max + 1);
@@ -409,7 +412,14 @@ extern "C" int pc_server_submit(pc_server* s, int kind, uint64_t x, uint64_t a, 
         std::lock_guard<std::mutex> g(s->mu);
         if (s->stop) return PC_EINVAL;
         rq.r.t_submit_ms = s->now_ms();
-        s->queue.push_back(rq);
+        if (s->policy == PC_SERVE_SMALL_FIRST) {
+            // ordered by x (the work grows with x), arrival order among equals
+            auto at = std::upper_bound(s->queue.begin(), s->queue.end(), rq,
+                                       [](const Request& a, const Request& b) { return a.r.x < b.r.x; });
+            s->queue.insert(at, rq);
+        } else {
+            s->queue.push_back(rq);
+        }
         s->pending++;
         s->st.submitted++;
     }

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
         return tot;
     };
     i64 acc = 0;
-    unsigned long long nleaves = 0, nclears = 0;
+    unsigned long long nleaves = 0, nclears = 0, nbusy = 0, nleafy = 0;
 
     for (;;) {
         __syncthreads();
@@ -328,6 +328,8 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                     }
                 }
             };
+            nbusy += __popcll(busy);
+            nleafy += __popcll(leafy);
             if (leafy) prefetch(__ffsll((long long)leafy) - 1);
             __syncwarp();
             const u32 cnt0 = cnt;
@@ -531,6 +533,8 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
     }
     if (lane == 0 && nleaves) atomicAdd(A.stat, nleaves);
     if (lane == 0 && nclears) atomicAdd(A.stat + 1, nclears);
+    if (lane == 0 && nbusy) atomicAdd(A.stat + 2, nbusy);     // busy (warp, step) pairs
+    if (lane == 0 && nleafy) atomicAdd(A.stat + 3, nleafy);   // of which with leaves
 }
 
 // ---------------------------------------------------------- schedule
@@ -859,8 +863,10 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     PC_TRY(reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out));
     PC_TRY(reduce_i128(ctx, A.acc, ctas, out));
 
-    u64 nl[2] = {0, 0};
-    PC_TRY(copy_to_host(ctx, nl, A.stat, 2 * sizeof(u64)));
+    u64 nl[4] = {0, 0, 0, 0};
+    PC_TRY(copy_to_host(ctx, nl, A.stat, 4 * sizeof(u64)));
+    ctx->stats.warp_steps += nl[2];
+    ctx->stats.leaf_warp_steps += nl[3];
     float ms = 0;
     PC_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
     ctx->stats.ms_hard_sieve = ms;

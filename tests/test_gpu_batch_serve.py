@@ -151,3 +151,19 @@ def test_autotune_keeps_results(alone):
     with pc.Context(0, alpha=3) as cx:
         cx.autotune(10 ** 9, 10 ** 10, reps=1)
         assert cx.tuned(5 * 10 ** 9)[0] == 3
+
+
+def test_server_small_first_policy(alone):
+    xs = [10 ** 13, 10 ** 9 + 7, 10 ** 12, 10 ** 10, 3 * 10 ** 11, 10 ** 9, 2 * 10 ** 12, 5 * 10 ** 10]
+    with pc.Context(0, streams=1) as cx:
+        with pc.Server(cx, x_max=10 ** 13, policy=pc.PC_SERVE_SMALL_FIRST) as srv:
+            for k, x in enumerate(xs):
+                srv.submit(pc.PC_QUERY_PI, x, 0, tag=k)
+            res = _drain(srv, len(xs))
+            st = srv.stats()
+    assert st["max_running"] == 1
+    order = sorted(res, key=lambda r: r["t_start_ms"])
+    later = [r["x"] for r in order[1:]]          # all queued while the first one ran
+    assert later == sorted(later)
+    for r in res:
+        assert r["value"] == alone.pi_count(r["x"])
