@@ -184,3 +184,41 @@ def test_full_size_pins(pi_pow10, pi_pow2):
         h = cx.s2_hard(10 ** 18, y, 5)
     with pc.Context(0, seg_bytes=32768, ctas_per_sm=1) as cx:
         assert cx.s2_hard(10 ** 18, y, 5) == h
+
+
+def _phi_wheel(x, a):
+    """phi(x, a) for a <= 7 from the textbook periodicity: with P the product of
+    the first a primes, phi(x, a) = (x // P) * phi(P, a) + phi(x mod P, a)."""
+    ps = [2, 3, 5, 7, 11, 13, 17][:a]
+    P = 1
+    for p in ps:
+        P *= p
+    r = x % P
+    ok = [all(n % p for p in ps) for n in range(1, P + 1)]
+    return (x // P) * sum(ok) + sum(ok[:r])
+
+
+def test_full_size_phi_properties(pi_pow10):
+    # properties that hold at any size, at the largest x of the benchmark
+    x = 10 ** 18
+    with pc.Context(0) as cx:
+        for a in (1, 3, 5, 7):
+            assert cx.phi(x, a) == _phi_wheel(x, a), a
+        for a in (100, 1000):
+            pa = o.nth_prime(a)
+            assert cx.phi(x, a) == cx.phi(x, a - 1) - cx.phi(x // pa, a - 1), a
+        # a >= pi(isqrt x): phi(x, a) = pi(x) - a + 1 (Section 4)
+        a = 50847534 + 10   # pi(10^9) + 10
+        assert cx.phi(x, a) == pi_pow10[18] - a + 1
+
+
+def test_largest_x_is_consistent():
+    # x = 2^63 - 1, the top of the domain: every alpha and segment size must agree
+    x = (1 << 63) - 1
+    with pc.Context(0) as cx:
+        v = cx.pi_count(x, 0)
+        assert cx.pi_count(x, 12) == v
+    with pc.Context(0, seg_bytes=65536) as cx:
+        assert cx.pi_count(x, 30) == v
+    with pc.Context(0) as cx:
+        assert cx.pi_count(1 << 62, 0) < v
