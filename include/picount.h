@@ -122,6 +122,21 @@ int pc_phi(pc_ctx* ctx, uint64_t x, uint64_t a, uint64_t* out_phi);
  * PC_EINVAL.  *out receives the exact signed 128-bit sum. */
 int pc_s2_hard(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, pc_i128* out);
 
+/* Shard k of n of S2_hard(x, y, c): the hard special leaves whose u falls in
+ * the k-th of n equal runs of sieve segments, plus (k = 0 only) the
+ * closed-form leaves with b <= 3.  The n shards are independent -- no shard
+ * needs another's counts -- because each starts its carries from the
+ * starting values phi(L - 1, b) of Section 4 (pc_phi_starts), and their sum
+ * is exactly pc_s2_hard(x, y, c).  Same domain as pc_s2_hard; 0 <= k < n. */
+int pc_s2_hard_shard(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, uint32_t k, uint32_t n, pc_i128* out);
+
+/* Starting values of Section 4: out[b - c] = phi(m, b) for every
+ * c <= b <= b_max, from phi(m, c) and the recurrence (4.1), the subtracted
+ * terms phi(m / p_b, b - 1) taken as 0, 1, Legendre's pi(m / p_b) - b + 2
+ * (when m / p_b < p_b^2) or a phi computation, as the paper's case split
+ * prescribes.  c <= 7; out has b_max - c + 1 entries. */
+int pc_phi_starts(pc_ctx* ctx, uint64_t m, uint32_t c, uint64_t b_max, uint64_t* out);
+
 /* P2(x, a) with a = pi(y): sum over primes y < p <= isqrt(x) of
  * (pi(x / p) - pi(p) + 1).  Requires iroot3(x) <= y <= isqrt(x).
  * The value fits in uint64_t for x < 2^63. */

@@ -20,7 +20,8 @@ ERRORS = {-1: "PC_EINVAL", -2: "PC_ERANGE", -3: "PC_ENOMEM", -4: "PC_ECUDA", -5:
 SYMBOLS = ["pc_create", "pc_destroy", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
            "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats", "pc_strerror", "pc_last_error", "pc_version",
            "pc_p2_noalloc", "pc_server_create", "pc_server_submit", "pc_server_poll", "pc_server_get_stats",
-           "pc_server_footprint", "pc_server_destroy", "pc_autotune", "pc_tuned"]
+           "pc_server_footprint", "pc_server_destroy", "pc_autotune", "pc_tuned", "pc_s2_hard_shard",
+           "pc_phi_starts"]
 
 PC_QUERY_PI = 0
 PC_QUERY_PHI = 1
@@ -113,12 +114,15 @@ def lib():
             L.pc_server_footprint.argtypes = [p, ctypes.c_int, u64, u64]
             L.pc_server_footprint.restype = u64
             L.pc_autotune.argtypes = [p, u64, u64, u32]
+            L.pc_s2_hard_shard.argtypes = [p, u64, u64, u32, u32, u32, ctypes.POINTER(PcI128)]
+            L.pc_phi_starts.argtypes = [p, u64, u32, u64, ctypes.POINTER(u64)]
             L.pc_tuned.argtypes = [p, u64, ctypes.POINTER(u32), ctypes.POINTER(u32)]
             L.pc_server_destroy.argtypes = [p]
             L.pc_server_destroy.restype = None
             for name in ("pc_create", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
                          "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats", "pc_server_create",
-                         "pc_server_submit", "pc_server_poll", "pc_server_get_stats", "pc_autotune", "pc_tuned"):
+                         "pc_server_submit", "pc_server_poll", "pc_server_get_stats", "pc_autotune", "pc_tuned",
+                         "pc_s2_hard_shard", "pc_phi_starts"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -181,6 +185,16 @@ class Context:
         out = PcI128()
         self._check(self._L.pc_s2_hard(self._h, x, y, c, ctypes.byref(out)))
         return out.value()
+
+    def s2_hard_shard(self, x: int, y: int, c: int, k: int, n: int) -> int:
+        out = PcI128()
+        self._check(self._L.pc_s2_hard_shard(self._h, x, y, c, k, n, ctypes.byref(out)))
+        return out.value()
+
+    def phi_starts(self, m: int, c: int, b_max: int) -> list:
+        out = (ctypes.c_uint64 * (b_max - c + 1))()
+        self._check(self._L.pc_phi_starts(self._h, m, c, b_max, out))
+        return list(out)
 
     def p2(self, x: int, y: int) -> int:
         out = ctypes.c_uint64()

@@ -537,3 +537,99 @@ extern "C" int pc_tuned(pc_ctx* ctx, uint64_t x, uint32_t* alpha, uint32_t* seg_
     *seg_bytes = ctx->params.seg_bytes ? ctx->params.seg_bytes : (ctx->tuned_seg[d] ? ctx->tuned_seg[d] : 32768);
     return PC_OK;
 }
+
+// ------------------------------------------------------- starting values
+// phi(m, b) for every c <= b <= b_max, by the recurrence (4.1)
+//   phi(m, b) = phi(m, b-1) - phi(m / p_b, b-1)
+// with the case split of Section 4 for the subtracted term, v = m / p_b:
+//   p_b > m:               phi(v, b-1) = phi(0, b-1) = 0;
+//   sqrt(m) < p_b <= m:    v < p_b, only 1 survives: phi(v, b-1) = 1;
+//   v < p_b^2 (Legendre):  every composite <= v has a prime factor < p_b, so
+//                          phi(v, b-1) = pi(v) - (b - 1) + 1, pi(v) from the pi table;
+//   otherwise:             phi(v, b-1) by the combinatorial algorithm (pc_phi),
+//                          these queries running concurrently on the worker slots.
+// The first value phi(m, c) is itself a pc_phi query.
+int phi_starts(pc_ctx* ctx, u64 m, u32 c, u64 b_max, u64* out)
+{
+    if (ctx->borrowed || c > b_max) return PC_EINVAL;
+    const u64 n = b_max - c + 1;
+    if (m == 0) {
+        for (u64 i = 0; i < n; i++) out[i] = 0;
+        return PC_OK;
+    }
+    // p_1 .. p_{b_max} on the host
+    const u64 r = pc_isqrt(m);
+    {
+        // p_b <= b (ln b + ln ln b) for b >= 6 (Rosser); only sizes the prime table
+        const double bb = (double)pc_max(b_max, (u64)6);
+        const u64 plim = (u64)(bb * (std::log(bb) + std::log(std::log(bb)))) + 64;
+        PC_TRY(tables_ensure(ctx, pc_max(plim + 4096, pc_iroot3(m) * pc_iroot3(m) + 4096), plim, 0, 7));
+    }
+    if (ctx->T.nprimes < b_max) {
+        pc_set_error(ctx, "phi starts: %llu primes needed", (unsigned long long)b_max);
+        return PC_EINVAL;
+    }
+    std::vector<u32> P(b_max + 1);
+    PC_CUDA(ctx, cudaMemcpy(P.data(), ctx->T.primes.p, (b_max + 1) * sizeof(u32), cudaMemcpyDeviceToHost));
+    // classify every term
+    std::vector<u64> term(n, 0), lv, lb;
+    std::vector<Query> q;
+    std::vector<u64> qb;
+    q.push_back(Query{PC_QUERY_PHI, m, c});   // phi(m, c)
+    qb.push_back(0);
+    for (u64 b = (u64)c + 1; b <= b_max; b++) {
+        const u64 p = P[b];
+        if (p > m) {
+            term[b - c] = 0;
+        } else if (p > r) {
+            term[b - c] = 1;
+        } else {
+            const u64 v = m / p;
+            if (v < p * p) {
+                lv.push_back(v);
+                lb.push_back(b);
+            } else {
+                q.push_back(Query{PC_QUERY_PHI, v, b - 1});
+                qb.push_back(b);
+            }
+        }
+    }
+    // Legendre terms from the pi table
+    if (!lv.empty()) {
+        u64 vmax = 0;
+        for (u64 v : lv) vmax = pc_max(vmax, v);
+        PC_TRY(tables_ensure(ctx, vmax, 64, 0, 7));
+        std::vector<u64> pv(lv.size());
+        PC_TRY(tables_pi_many(ctx, lv.data(), pv.data(), lv.size()));
+        for (size_t i = 0; i < lv.size(); i++) term[lb[i] - c] = pv[i] - lb[i] + 2;
+    }
+    // combinatorial terms, concurrently
+    TableNeeds N;
+    for (const Query& qq : q) {
+        const u64 a = qq.a;
+        if (a == 0) continue;
+        const u64 pa = P[a], pa1 = a + 1 <= b_max ? P[a + 1] : ~0ull;
+        needs_phi(ctx, qq.x, a, pa, pa1 == ~0ull ? pc_isqrt(qq.x) + 1 : pa1, N);
+    }
+    PC_TRY(build_needs(ctx, N));
+    std::vector<u64> qv(q.size(), 0);
+    const pc_stats keep = ctx->stats;   // the queries run on the worker slots; keep the caller's counters
+    const int rq = run_queries(ctx, q, qv);
+    ctx->stats = keep;
+    PC_TRY(rq);
+    for (size_t i = 1; i < q.size(); i++) term[qb[i] - c] = qv[i];
+    out[0] = qv[0];
+    for (u64 i = 1; i < n; i++) out[i] = out[i - 1] - term[i];
+    return PC_OK;
+}
+
+extern "C" int pc_phi_starts(pc_ctx* ctx, uint64_t m, uint32_t c, uint64_t b_max, uint64_t* out)
+{
+    if (!ctx || !out || c > 7 || b_max < c) return PC_EINVAL;
+    if (m >> 63) return PC_ERANGE;
+    PC_CUDA(ctx, cudaSetDevice(ctx->device));
+    std::vector<u64> v(b_max - c + 1);
+    PC_TRY(phi_starts(ctx, m, c, b_max, v.data()));
+    memcpy(out, v.data(), v.size() * sizeof(u64));
+    return PC_OK;
+}

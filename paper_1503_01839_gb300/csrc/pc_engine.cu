@@ -79,7 +79,7 @@ extern "C" void pc_destroy(pc_ctx* ctx)
     workers_destroy(ctx);
     DevBuf* bufs[] = {&ctx->seg_b, &ctx->seg_off, &ctx->counts, &ctx->tallies,
                       &ctx->acc_seg, &ctx->partials, &ctx->result, &ctx->misc, &ctx->scan_tmp, &ctx->queue,
-                      &ctx->easy_rng, &ctx->easy_chunk_off, &ctx->easy_cmap};
+                      &ctx->easy_rng, &ctx->easy_chunk_off, &ctx->easy_cmap, &ctx->starts};
     for (DevBuf* b : bufs) buf_free(*b);
     if (!ctx->borrowed) {
         Tables& T = ctx->T;
@@ -276,7 +276,21 @@ extern "C" int pc_leaf_sums(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, uin
     return PC_OK;
 }
 
+static int s2_hard_impl(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, u32 shard_k, u32 shard_n, pc_i128* out);
+
 extern "C" int pc_s2_hard(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, pc_i128* out)
+{
+    return s2_hard_impl(ctx, x, y, c, 0, 0, out);
+}
+
+extern "C" int pc_s2_hard_shard(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, uint32_t k, uint32_t n,
+                                pc_i128* out)
+{
+    if (n == 0 || k >= n) return PC_EINVAL;
+    return s2_hard_impl(ctx, x, y, c, k, n, out);
+}
+
+static int s2_hard_impl(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, u32 shard_k, u32 shard_n, pc_i128* out)
 {
     if (!ctx || !out) return PC_EINVAL;
     if (x >> 63) return PC_ERANGE;
@@ -299,6 +313,8 @@ extern "C" int pc_s2_hard(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, pc_i1
     }
     PC_TRY(sync_timed(ctx, &ctx->stats.ms_tables, ph));
     LeafProblem P{x, y, z, c, piy, false, piy, B};
+    P.shard_k = shard_k;
+    P.shard_n = shard_n;
     ctx->stats.y = y;
     ctx->stats.z = z;
     ctx->stats.a = piy;
@@ -306,7 +322,8 @@ extern "C" int pc_s2_hard(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, pc_i1
     ctx->stats.c = c;
     I128Pair* d;
     PC_TRY(result_slots(ctx, 1, &d));
-    PC_TRY(run_hard_smallb(ctx, P, d));
+    if (shard_n == 0 || shard_k == 0)
+        PC_TRY(run_hard_smallb(ctx, P, d));   // closed-form leaves (b <= 3): counted once, in shard 0
     PC_TRY(run_hard_sieve(ctx, P, d));
     i128 v;
     PC_TRY(read_slots(ctx, 1, &v));

@@ -57,6 +57,7 @@ struct HardArgs {
     u64 a;
     bool trunc;
     u64 nseg;
+    u64 s0, s1;   // the segments [s0, s1) of this run (a shard, or all of them)
     u32 seg_bytes, sub_bytes, nw, sub_shift;   // sub_bits = 1 << sub_shift
     u64 span;     // integers per segment
     u64 dspan;    // integers per sub-range
@@ -69,6 +70,7 @@ struct HardArgs {
     const u32* segB;
     const u64* rcp_seg;   // per segment: reciprocals of L_s and L_s + span (0 for L = 0)
     const u64* off;
+    const u64* start;   // phi(L_{s0} - 1, b) for b = k0 .. bmax (index b - k0), or null for s0 = 0
     u32* counts;
     i32* tallies;
     const HardItem* items;
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
         if (tid == 0 && rep == 0) {
             u32 t = 0;
             for (u32 k = 0; k < nw; k++) t += prev[k];
-            A.counts[A.off[0] + s] = t;
+            A.counts[A.off[0] + (s - A.s0)] = t;
         }
 
         for (u32 bb = A.k0 + 1; bb <= Bs; bb += BATCH) {
@@ -422,8 +424,8 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                             one_leaf(info, m32, v, gpf);
                         }
                         tl = __reduce_add_sync(0xffffffffu, (u32)tl);
+                        if (lane == 0) tw[t * nw + w] = tl;   // steps without leaves keep the 0 set above
                     }
-                    if (lane == 0) tw[t * nw + w] = tl;
                 }
                 if (b < Bs) {
                     const u32 p = st[t].p;
@@ -506,7 +508,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 u32 C = 0;
                 for (u32 k = 0; k < nw; k++) C += cw[t * nw + k];
                 const u64 row = st[t].row;
-                if (rep == 0 && b < Bs) A.counts[row + s] = C;
+                if (rep == 0 && b < Bs) A.counts[row + (s - A.s0)] = C;
                 if (b > A.kleaf) {
                     const u32* cp = t ? cw + (t - 1) * nw : prev;
                     i32 T = 0;
@@ -517,7 +519,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         intra += (i64)tk * run;
                         run += cp[k];
                     }
-                    if (T) atomicAdd(&A.tallies[row + s], T);
+                    if (T) atomicAdd(&A.tallies[row + (s - A.s0)], T);
                     acc += intra;
                 }
             }
@@ -554,8 +556,8 @@ __global__ void seg_b_kernel(u64 x, u64 nseg, u64 span, u32 bmax, PiTable pit, u
     segB[s] = B;
 }
 
-// S_b = number of segments with B_s >= b (B_s is non-increasing in s)
-__global__ void row_len_kernel(const u32* segB, u64 nseg, u32 k0, u32 bmax, u32* len)
+// S_b = number of segments in [s0, s1) with B_s >= b (B_s is non-increasing in s)
+__global__ void row_len_kernel(const u32* segB, u64 nseg, u64 s0, u64 s1, u32 k0, u32 bmax, u32* len)
 {
     u32 t = blockIdx.x * blockDim.x + threadIdx.x;
     u32 b = k0 + t;
@@ -565,7 +567,7 @@ __global__ void row_len_kernel(const u32* segB, u64 nseg, u32 k0, u32 bmax, u32*
         u64 mid = (lo + hi) >> 1;
         if (segB[mid] >= b) lo = mid + 1; else hi = mid;
     }
-    len[t] = (u32)lo;
+    len[t] = (u32)(pc_min(pc_max(lo, s0), s1) - s0);
 }
 
 // Upper bound of the hard leaves of every segment (the lpf filter of the
@@ -580,7 +582,7 @@ __global__ void hard_estimate_kernel(HardArgs A, u64 total, u32 nrows, unsigned 
         }
         const u64 b = A.k0 + lo;
         if (b <= A.kleaf || b > A.a) continue;
-        const u64 s = e - A.off[lo];
+        const u64 s = A.s0 + (e - A.off[lo]);
         const u64 L = s * A.span;
         const u64 p = A.primes[b];
         const u64 vp = A.primes_rcp[b];
@@ -613,7 +615,7 @@ __global__ void __launch_bounds__(NT) hard_combine_kernel(HardArgs A, I128Pair* 
         const u64 row = A.off[b - A.k0];
         const u64 Sb = A.off[b - A.k0 + 1] - row;
         const u64 prow = A.off[b - 1 - A.k0];
-        if (threadIdx.x == 0) s_carry = 0;
+        if (threadIdx.x == 0) s_carry = A.start ? A.start[b - 1 - A.k0] : 0;
         __syncthreads();
         for (u64 base = 0; base < Sb; base += NT) {
             const u64 s = base + threadIdx.x;
@@ -680,13 +682,13 @@ static u32 pc_sub_bytes(pc_ctx* ctx, u32 seg_bytes)
 // span * 8/30 * sum_{13 <= p <= P} 1/p ~ span * 8/30 * (ln ln P - 1.0056),
 // P = isqrt(x / L), the largest prime the segment sieves with.
 static void plan_items(const std::vector<u32>& segB, const std::vector<unsigned long long>& est, u32 k0, int ctas,
-                       u64 x, u64 z, u64 span, std::vector<HardItem>& items)
+                       u64 x, u64 z, u64 span, u64 s0, u64 s1, std::vector<HardItem>& items)
 {
     const double STEP_COST = 128.0, CLEAR_COST = 0.08;
     const size_t nseg = segB.size();
     std::vector<double> base(nseg);
     double total = 0;
-    for (size_t s = 0; s < nseg; s++) {
+    for (size_t s = s0; s < s1; s++) {
         const double steps = segB[s] > k0 ? (double)(segB[s] - k0) : 0.0;
         const u64 P = s ? pc_min(pc_isqrt(x / (s * span)), pc_isqrt(z)) : pc_isqrt(z);
         const double ll = P > 16 ? std::log(std::log((double)P)) - 1.0056 : 0.0;
@@ -695,8 +697,8 @@ static void plan_items(const std::vector<u32>& segB, const std::vector<unsigned 
     }
     const double target = std::max(total / (ctas * 4.0), 1.0);
     std::vector<std::pair<double, HardItem>> v;
-    v.reserve(nseg + 64);
-    for (size_t s = 0; s < nseg; s++) {
+    v.reserve(s1 - s0 + 64);
+    for (size_t s = s0; s < s1; s++) {
         if (segB[s] <= k0) continue;
         u32 R = 1;
         if (base[s] + (double)est[s] > target && (double)est[s] > base[s]) {
@@ -736,6 +738,20 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     A.span = 30ull * A.seg_bytes;
     A.dspan = 30ull * A.sub_bytes;
     A.nseg = P.z / A.span + 1;
+    A.s0 = 0;
+    A.s1 = A.nseg;
+    std::vector<u64> hstart;
+    if (P.shard_n) {
+        A.s0 = A.nseg * P.shard_k / P.shard_n;
+        A.s1 = A.nseg * (P.shard_k + 1) / P.shard_n;
+        if (A.s1 <= A.s0) return PC_OK;   // an empty shard
+        if (A.s0) {
+            // carries into the shard: phi(L - 1, b) for every b (Section 4), computed
+            // before this run claims the context's scratch
+            hstart.resize(bmax - A.k0 + 1);
+            PC_TRY(phi_starts(ctx, A.s0 * A.span - 1, A.k0, bmax, hstart.data()));
+        }
+    }
     A.pit = ctx->T.pi();
     A.rk = ctx->T.rank();
     A.ml = ctx->T.mlist();
@@ -755,12 +771,20 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     seg_b_kernel<<<(unsigned)((A.nseg + 255) / 256), 256, 0, ctx->stream>>>(P.x, A.nseg, A.span, A.bmax, A.pit, segB,
                                                                             rcp_seg);
     PC_LAUNCHED(ctx);
-    row_len_kernel<<<(unsigned)((nrows + 255) / 256), 256, 0, ctx->stream>>>(segB, A.nseg, A.k0, A.bmax, rowlen);
+    row_len_kernel<<<(unsigned)((nrows + 255) / 256), 256, 0, ctx->stream>>>(segB, A.nseg, A.s0, A.s1, A.k0, A.bmax,
+                                                                              rowlen);
     PC_LAUNCHED(ctx);
     ctx->stats.kernel_launches += 2;
     PC_TRY(scan_exclusive_u32_to_u64(ctx, rowlen, off, nrows));
     A.segB = segB;
     A.off = off;
+    A.start = nullptr;
+    if (!hstart.empty()) {
+        PC_TRY(buf_reserve(ctx, ctx->starts, hstart.size() * sizeof(u64)));
+        PC_CUDA(ctx, cudaMemcpyAsync(ctx->starts.p, hstart.data(), hstart.size() * sizeof(u64),
+                                     cudaMemcpyHostToDevice, ctx->stream));
+        A.start = ctx->starts.as<u64>();
+    }
     u64 total = 0;
     PC_TRY(copy_to_host(ctx, &total, off + nrows, sizeof(u64)));
     if (total >> 32) {
@@ -827,7 +851,7 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     int ctas = ctx->sm_count * per_sm;
 
     std::vector<HardItem> items;
-    plan_items(hsegB, hest, A.k0, ctas, P.x, P.z, A.span, items);
+    plan_items(hsegB, hest, A.k0, ctas, P.x, P.z, A.span, A.s0, A.s1, items);
     A.nitems = items.size();
     ctx->stats.work_items = items.size();
     for (const HardItem& it : items) ctx->stats.item_steps += hsegB[it.s] > A.k0 ? hsegB[it.s] - A.k0 : 0;

@@ -86,7 +86,7 @@ struct pc_ctx {
     Tables T;
     // scratch (grow-only)
     DevBuf seg_b, seg_off, counts, tallies, acc_seg, partials, result, misc, scan_tmp, queue;
-    DevBuf easy_rng, easy_chunk_off, easy_cmap;
+    DevBuf easy_rng, easy_chunk_off, easy_cmap, starts;
     // pinned host staging for small results
     void* host_stage = nullptr;
     pc_stats stats{};
@@ -134,6 +134,8 @@ int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 
 int tables_phi_c(pc_ctx* ctx, u32 c);   // phi(., c) residue table
 // values of pi(v) for a handful of v (v <= pi_limit), synchronizing
 int tables_pi_values(pc_ctx* ctx, const u64* v, u64* out, int n);
+// pi(v) for any number of v (every v <= the table limit), synchronizing
+int tables_pi_many(pc_ctx* ctx, const u64* v, u64* out, size_t n);
 
 // ----------------------------------------------------------------- leaves
 struct LeafProblem {
@@ -143,7 +145,15 @@ struct LeafProblem {
     bool trunc;   // a < pi(y): filter gpf(m) <= p_a
     u64 piy;      // pi(y)
     u64 B;        // pi(isqrt z)
+    // hard-leaf sieve over segments [shard_k * nseg / shard_n, (shard_k + 1) * nseg / shard_n) only
+    // (shard_n = 0: all of them); the leaves' carries then start from phi(L - 1, b)
+    u32 shard_k = 0, shard_n = 0;
 };
+
+// phi(m, b) for every c <= b <= b_max (Section 4 starting values): out[b - c]
+int phi_starts(pc_ctx* ctx, u64 m, u32 c, u64 b_max, u64* out);
+// segments of the hard-leaf sieve for (x, z) in the context's geometry
+u64 hard_segments(pc_ctx* ctx, u64 z);
 
 // Each adds its sum to *out (device I128Pair) -- out must be zeroed first.
 int run_s1(pc_ctx* ctx, const LeafProblem& P, I128Pair* out);

@@ -481,6 +481,41 @@ int tables_pi_values(pc_ctx* ctx, const u64* v, u64* out, int n)
     return copy_to_host(ctx, out, d + 32, n * sizeof(u64));
 }
 
+__global__ void pi_many_kernel(PiTable t, const u64* v, u64* out, u64 n)
+{
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = pi_lookup(t, v[i]);
+}
+
+int tables_pi_many(pc_ctx* ctx, const u64* v, u64* out, size_t n)
+{
+    if (n == 0) return PC_OK;
+    for (size_t i = 0; i < n; i++)
+        if (v[i] > ctx->T.pi_limit) {
+            pc_set_error(ctx, "pi lookup %llu beyond table %llu", (unsigned long long)v[i],
+                         (unsigned long long)ctx->T.pi_limit);
+            return PC_EINVAL;
+        }
+    DevBuf tmp;
+    int rc = buf_reserve(ctx, tmp, 2 * n * sizeof(u64));
+    if (rc != PC_OK) return rc;
+    u64* d = tmp.as<u64>();
+    cudaError_t e = cudaMemcpyAsync(d, v, n * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        pi_many_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->T.pi(), d, d + n, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + n, n * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    buf_free(tmp);
+    ctx->stats.kernel_launches++;
+    if (e != cudaSuccess) {
+        pc_set_error(ctx, "pi lookups: %s", cudaGetErrorString(e));
+        return PC_ECUDA;
+    }
+    return PC_OK;
+}
+
 int tables_phi_c(pc_ctx* ctx, u32 c)
 {
     Tables& T = ctx->T;
