@@ -52,12 +52,12 @@ def workload():
     return {"x": X, "y": y, "c": C, "z": X // y}
 
 
-def config(seg_bytes):
+def config(seg_bytes, parallelism="replicas"):
     w = workload()
     return {"workload": "S2_hard hard-leaf sieve x=%.0e y=%d*iroot3(x)=%d c=%d (one evaluation per step)"
                         % (w["x"], ALPHA, w["y"], C),
             "x": w["x"], "y": w["y"], "z": w["z"], "c": C, "seg_bytes": seg_bytes,
-            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": parallelism}
 
 
 def dist_env():
@@ -307,6 +307,16 @@ def max_over_ranks(v, world):
     return float(t[0])
 
 
+def sum_over_ranks(v, world):
+    """Exact sum of a Python int (any size, e.g. a 128-bit partial sum) over ranks."""
+    if world <= 1:
+        return v
+    import torch
+    parts = [None] * world
+    torch.distributed.all_gather_object(parts, int(v))
+    return sum(parts)
+
+
 def job_throughput(units_per_rank, world, seconds):
     """Whole-job throughput of `world` replicas that each processed
     units_per_rank units, timed by the slowest one."""
@@ -330,6 +340,8 @@ def main():
     ap.add_argument("--serve", type=int, default=1000, help="requests of the served workload (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--streams", type=int, default=8, help="query slots of the batched/served forms")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: split one S2_hard into N independent shards instead of N replicas")
     args = ap.parse_args()
     global X, ALPHA
     X, ALPHA = int(args.x), args.alpha
@@ -362,10 +374,15 @@ def main():
     ctx.set_stream(stream.cuda_stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
+    # one step: the whole S2_hard on every rank (replicas), or with --shard
+    # rank r's shard of it (Section 4 starting values, no exchange of counts)
+    shard = args.shard and world > 1
+    step = (lambda x_, y_, c_: ctx.s2_hard_shard(x_, y_, c_, rank, world)) if shard else ctx.s2_hard
+
     # warm-up (also builds the device tables for this x)
     ref = None
     for _ in range(max(1, args.warmup)):
-        v = ctx.s2_hard(x, y, c)
+        v = step(x, y, c)
         ref = v if ref is None else ref
         assert v == ref, "S2_hard changed between runs"
     torch.cuda.synchronize()
@@ -383,7 +400,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            v = ctx.s2_hard(x, y, c)
+            v = step(x, y, c)
             e1.record(stream)
             assert v == ref
             evs.append((e0, e1))
@@ -393,7 +410,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in evs]
     tot_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = tot_ms / args.steps
-    value = job_throughput(z, world, ms_per_step / 1000.0)
+    # shards split one z among the ranks; replicas each sieve all of it
+    value = job_throughput(z, 1 if shard else world, ms_per_step / 1000.0)
 
     # end to end through the C ABI: host scalars in, host int128 out
     e2e_times = []
@@ -401,7 +419,7 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        v = ctx.s2_hard(x, y, c)
+        v = step(x, y, c)
         e2e_times.append(time.perf_counter() - t0)
         assert v == ref
     e2e_s = max_over_ranks(statistics.mean(e2e_times), world)
@@ -423,9 +441,9 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": config(int(st["seg_bytes"])),
-            "e2e": {"value": job_throughput(z, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 24, "d2h_bytes_per_step": 16},
+            "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": config(int(st["seg_bytes"]), "shards (Section 4 starting values)" if shard else "replicas"),
+            "e2e": {"value": job_throughput(z, 1 if shard else world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 24, "d2h_bytes_per_step": 16},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G smem-bank-accesses/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -433,7 +451,8 @@ def main():
                          "peak_basis": "32 banks x %d SMs x %.0f MHz (max SM clock, MEASURED_PEAKS.json)"
                                        % (n_sm, sm_max_mhz)},
             "clocks": clk.summary(),
-            "s2_hard": str(ref), "hard_leaves": int(st["hard_leaves"]), "clears": int(st["clears"]),
+            "s2_hard": str(sum_over_ranks(ref, world) if shard else ref),
+            "hard_leaves": int(st["hard_leaves"]), "clears": int(st["clears"]),
             "hard_leaves_per_s": float(st["hard_leaves"]) / (ms_per_step / 1000.0),
             "segments": int(st["segments"]), "steps_seg_prime": int(st["steps"]),
             "timed_wall_s": t_wall}

@@ -34,7 +34,9 @@ def _rank_main(rank, world, port, q):
         value = oracle.pi_sieve(units)
         slowest = bench.max_over_ranks(local_ms, world)
         thr = bench.job_throughput(units, world, slowest / 1000.0)
-        q.put((rank, slowest, thr, value))
+        # shard partial sums are 128-bit integers: their sum over ranks must be exact
+        total = bench.sum_over_ranks((rank + 1) * (1 << 100) - rank, world)
+        q.put((rank, slowest, thr, value, total))
     finally:
         dist.destroy_process_group()
 
@@ -51,10 +53,11 @@ def test_replicas_max_over_ranks_gloo():
         p.join(120)
         assert p.exitcode == 0
     res = sorted(q.get(timeout=5) for _ in range(2))
-    for rank, slowest, thr, value in res:
+    for rank, slowest, thr, value, total in res:
         assert slowest == 150.0                       # every rank sees the slowest replica's time
         assert thr == pytest.approx(2 * 10 ** 6 / 0.150)
         assert value == 78498                          # pi(10^6), Table 1
+        assert total == 3 * (1 << 100) - 1
     assert res[0][1:] == res[1][1:]
 
 
