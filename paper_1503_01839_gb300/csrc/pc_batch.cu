@@ -485,7 +485,7 @@ extern "C" int pc_autotune(pc_ctx* ctx, uint64_t x_lo, uint64_t x_hi, uint32_t r
         x = pc_min(pc_max(x, x_lo), x_hi);
         if (x < (1ull << 20) || decimal_digits(x) != d) continue;
         const u32 a0 = default_alpha(x);
-        u32 alphas[5] = {pc_max(1u, a0 / 2), pc_max(1u, (2 * a0) / 3), a0, (3 * a0 + 1) / 2, 2 * a0};
+        u32 alphas[5] = {a0 / 2 ? a0 / 2 : 1u, (2 * a0) / 3 ? (2 * a0) / 3 : 1u, a0, (3 * a0 + 1) / 2, 2 * a0};
         const u32 segs[3] = {16384, 32768, 65536};
         double best_ms = 1e300;
         u32 best_a = 0, best_s = 0;

@@ -823,9 +823,19 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     int per_sm = 0;
     for (const Variant& v : variants) {
         if (nt > v.maxt) continue;
-        cudaError_t ea = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // The limit is a property of the kernel, shared by every host thread of the
+        // process: always raise it to the device maximum (never to this call's size),
+        // so that a concurrent query with larger segments is not cut short.
+        cudaFuncAttributes fa;
+        PC_CUDA(ctx, cudaFuncGetAttributes(&fa, v.fn));
+        const size_t dyn_max = ctx->smem_optin - fa.sharedSizeBytes;
+        if (smem > dyn_max) {
+            pc_set_error(ctx, "hard-leaf sieve: %zu bytes of shared memory per CTA", smem);
+            return PC_EINVAL;
+        }
+        cudaError_t ea = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
         if (ea != cudaSuccess) {
-            pc_set_error(ctx, "cudaFuncSetAttribute(smem=%zu): %s", smem, cudaGetErrorString(ea));
+            pc_set_error(ctx, "cudaFuncSetAttribute(smem=%zu): %s", dyn_max, cudaGetErrorString(ea));
             return PC_ECUDA;
         }
         int fit = 0;   // resident CTAs the SM can hold (registers and shared memory)

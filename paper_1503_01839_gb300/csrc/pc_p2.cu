@@ -266,7 +266,16 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     A.queue = ctx->queue.as<u32>();
     const u32 nblk = A.seg_bytes >> 7;
     size_t smem = A.seg_bytes + (2 * (size_t)nblk + 2) * sizeof(u32);
-    cudaError_t e = cudaFuncSetAttribute(p2_sieve_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the kernel's limit is shared by every host thread: set the device maximum
+    cudaFuncAttributes fa;
+    PC_CUDA(ctx, cudaFuncGetAttributes(&fa, p2_sieve_kernel<512>));
+    const size_t dyn_max = ctx->smem_optin - fa.sharedSizeBytes;
+    if (smem > dyn_max) {
+        pc_set_error(ctx, "p2 sieve: %zu bytes of shared memory per CTA", smem);
+        return PC_EINVAL;
+    }
+    cudaError_t e = cudaFuncSetAttribute(p2_sieve_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dyn_max);
     if (e != cudaSuccess) {
         pc_set_error(ctx, "p2 smem attribute: %s", cudaGetErrorString(e));
         return PC_ECUDA;

@@ -167,3 +167,39 @@ def test_server_small_first_policy(alone):
     assert later == sorted(later)
     for r in res:
         assert r["value"] == alone.pi_count(r["x"])
+
+
+def test_concurrent_contexts_with_different_segments(alone):
+    # Per-kernel launch limits are process-wide: two host threads running
+    # queries with different segment sizes at once must not disturb each other.
+    import threading
+    x, y = 10 ** 14, 8 * 46415
+    want = alone.s2_hard(x, y, 5)
+    errors, results = [], []
+
+    def run(seg):
+        try:
+            with pc.Context(0, seg_bytes=seg) as cx:
+                for _ in range(6):
+                    results.append(cx.s2_hard(x, y, 5))
+                    results.append(cx.p2(x, y))
+        except Exception as e:   # collected and re-raised below
+            errors.append(e)
+
+    th = [threading.Thread(target=run, args=(seg,)) for seg in (16384, 65536, 131072)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
+    p2 = alone.p2(x, y)
+    assert all(r in (want, p2) for r in results) and results.count(want) == 18
+
+
+def test_batch_after_autotune_over_many_decades(alone):
+    # decades tuned to different segment sizes run concurrently in one batch
+    xs = inputs.log_uniform_x(200, 8.0, 14.0, seed=41)
+    with pc.Context(0, streams=8) as cx:
+        cx.autotune(min(xs), max(xs), reps=1)
+        got = cx.pi_count_batch(xs)
+    assert got == [alone.pi_count(x) for x in xs]
