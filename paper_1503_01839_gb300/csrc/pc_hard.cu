@@ -458,24 +458,53 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                                 i32 by = base + (i32)p * (i32)o + cj;
                                 if (o == 0 && r8(j) < kmod) by += step4;
                                 u32 n = 0;
-                                for (; by < (i32)sub_bytes; by += step4, n++) clear_bit(((u32)by << 3) + bj);
+                                // two rounds at a time, both words loaded before either is written
+                                // (they are 4p bytes apart, so never the same word)
+                                for (; by + step4 < (i32)sub_bytes; by += 2 * step4, n += 2) {
+                                    const u32 pa = ((u32)by << 3) + bj, pb = ((u32)(by + step4) << 3) + bj;
+                                    const u32 ma = 1u << (pa & 31), mb = 1u << (pb & 31);
+                                    const u32 oa = my[pa >> 5], ob = my[pb >> 5];
+                                    if (oa & ma) {
+                                        my[pa >> 5] = oa & ~ma;
+                                        dec++;
+                                        atomicSub(&myblk32[pa >> 9], 1u << (16 * ((pa >> 8) & 1)));
+                                    }
+                                    if (ob & mb) {
+                                        my[pb >> 5] = ob & ~mb;
+                                        dec++;
+                                        atomicSub(&myblk32[pb >> 9], 1u << (16 * ((pb >> 8) & 1)));
+                                    }
+                                }
+                                if (by < (i32)sub_bytes) {
+                                    clear_bit(((u32)by << 3) + bj);
+                                    n++;
+                                }
                                 nclears += n;
                             } else {
                                 const uint4 c0 = *(const uint4*)st[t].coff, c1 = *(const uint4*)(st[t].coff + 4);
                                 const u32 cw8[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-                                // lane = whole wheel rounds, even rounds first, then odd ones
+                                // lane = whole wheel rounds, even rounds first, then odd ones.
+                                // The blocks are recounted afterwards (p < RECOUNT_P), so a bit is
+                                // simply cleared; a lane takes rounds r and r + 64 together
+                                // (64 p bytes apart: never the same word) to overlap their loads.
                                 for (u32 ph = 0; ph < 2; ph++) {
-                                    for (u32 r = 2 * lane + ph;; r += 64) {
+                                    for (u32 r = 2 * lane + ph;; r += 128) {
                                         const i32 b0 = base + (i32)(p * r);
                                         if (b0 >= (i32)sub_bytes) break;
+                                        const i32 b1 = b0 + 64 * (i32)p;
 #pragma unroll
                                         for (int jj = 0; jj < 8; jj++) {
-                                            if (r == 0 && r8(jj) < kmod) continue;
-                                            const i32 by = b0 + (i32)cw8[jj];
-                                            if (by >= (i32)sub_bytes) break;
+                                            const i32 by0 = b0 + (i32)cw8[jj], by1 = b1 + (i32)cw8[jj];
+                                            const bool ok0 = by0 < (i32)sub_bytes && !(r == 0 && r8(jj) < kmod);
+                                            const bool ok1 = by1 < (i32)sub_bytes;
                                             const u32 bit = ((jj < 4 ? bv.x : bv.y) >> (8 * (jj & 3))) & 0xFFu;
-                                            clear_bit(((u32)by << 3) + bit);
-                                            nclears++;
+                                            const u32 q0 = ((u32)by0 << 3) + bit, q1 = ((u32)by1 << 3) + bit;
+                                            u32 w0 = 0, w1 = 0;
+                                            if (ok0) w0 = my[q0 >> 5];
+                                            if (ok1) w1 = my[q1 >> 5];
+                                            if (ok0) my[q0 >> 5] = w0 & ~(1u << (q0 & 31));
+                                            if (ok1) my[q1 >> 5] = w1 & ~(1u << (q1 & 31));
+                                            nclears += (u32)ok0 + (u32)ok1;
                                         }
                                     }
                                     __syncwarp();
