@@ -178,9 +178,10 @@ u32 default_alpha(u64 x)
     if (d <= 8) return 2;
     if (d == 9) return 4;
     if (d <= 11) return 6;
-    if (d <= 13) return 12;
+    if (d <= 13) return 24;
+    if (d <= 15) return 28;
     if (d <= 17) return 24;
-    return 40;
+    return 48;
 }
 
 int decimal_digits(u64 x)
