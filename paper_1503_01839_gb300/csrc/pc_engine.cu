@@ -87,6 +87,10 @@ extern "C" void pc_destroy(pc_ctx* ctx)
                           &T.ml_gpf, &T.ml_rcp, &T.rank_bits, &T.rank_cnt};
         for (DevBuf* b : tabs) buf_free(*b);
         for (int c = 0; c < 8; c++) buf_free(T.phiT[c]);
+        for (int k = 0; k < Tables::NSUB; k++) {
+            DevBuf* sb[] = {&T.sl_m[k], &T.sl_info[k], &T.sl_gpf[k], &T.sl_rcp[k], &T.sl_bits[k], &T.sl_cnt[k]};
+            for (DevBuf* b : sb) buf_free(*b);
+        }
     }
     if (ctx->ev_ok)
         for (int i = 0; i < 16; i++) cudaEventDestroy(ctx->ev[i]);

@@ -64,6 +64,12 @@ struct HardArgs {
     PiTable pit;
     RankTable rk;
     MList ml;
+    // sub-lists of the m-list (lpf index > slK[k]); a prime p_b reads its leaves
+    // from the last one with slK <= b, else from ml
+    MList sl[Tables::NSUB];
+    RankTable srk[Tables::NSUB];
+    u32 slK[Tables::NSUB];
+    u32 nsl;
     const u32* primes;
     const u64* primes_rcp;
     u64 rcp_y;          // floor((2^64 - 1) / y)
@@ -80,6 +86,10 @@ struct HardArgs {
     unsigned long long* stat;      // [0] hard leaves, [1] multiples crossed off
 };
 
+// field f of the m-list a step reads its leaves from (li from its flags)
+#define PC_LIST(A, li, f)                                                                                      \
+    ((li) == 0 ? (A).ml.f : (li) == 1 ? (A).sl[0].f : (li) == 2 ? (A).sl[1].f : (li) == 3 ? (A).sl[2].f : (A).sl[3].f)
+
 struct __align__(16) StepInfo {
     u64 xp;        // x / p_b
     u64 q;         // L / p_b
@@ -89,7 +99,7 @@ struct __align__(16) StepInfo {
     u32 r0;        // L mod p_b
     u32 coff[8];   // floor(p * R8[j] / 30): byte offset of class j inside a wheel round
     u8 cbit[8];    // bit of class j inside its byte
-    u32 flags;     // bit 0: leaves are primes, bit 1: step has leaves
+    u32 flags;     // bit 0: leaves are primes, bit 1: step has leaves, bits 2-4: m-list (0 = all, k = sub-list k-1)
     u32 pself;     // segment bit of p_b itself, or ~0
     u32 row;       // off[b - k0]: start of the count / tally rows of b
     u32 pad[3];
@@ -213,7 +223,12 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 si.mlo = si.mhi = 0;
                 si.pself = (p >= L && p < L + A.span) ? seg_pos(p, L) : ~0u;
                 if (b > A.kleaf && b <= A.a && leaf_window(A, p, vp, si.xp, L, rLk[0], rLk[nw], si.mlo, si.mhi))
-                    si.flags = 2u | (p * p > A.y ? 1u : 0u);
+                {
+                    u32 li = 0;
+                    for (u32 k = 0; k < A.nsl; k++)
+                        if (A.slK[k] <= b) li = k + 1;
+                    si.flags = 2u | (p * p > A.y ? 1u : 0u) | (li << 2);
+                }
                 for (int j = 0; j < 8; j++) {
                     const u32 pr = (u32)p * r8(j);
                     si.coff[j] = pr / 30;
@@ -236,7 +251,9 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         const u64 b = bb + t;
                         v32 = (u32)(pc_min(pc_max(pi_lookup(A.pit, v), b), A.a) + 1);
                     } else {
-                        v32 = (u32)rank_lookup(A.rk, v);
+                        const u32 li = (si.flags >> 2) & 7u;
+                        v32 = (u32)rank_lookup(li == 0 ? A.rk : li == 1 ? A.srk[0] : li == 2 ? A.srk[1]
+                                                                  : li == 3 ? A.srk[2] : A.srk[3], v);
                     }
                 }
                 I[idx] = v32;
@@ -323,10 +340,11 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         pf_v = A.primes_rcp[i];
                         pf_gpf = 0;
                     } else {
-                        pf_info = A.ml.info[i];
-                        pf_m = A.ml.m[i];
-                        pf_v = A.ml.rcp[i];
-                        pf_gpf = A.trunc ? A.ml.gpf[i] : 0;
+                        const u32 li = (st[t].flags >> 2) & 7u;
+                        pf_info = PC_LIST(A, li, info)[i];
+                        pf_m = PC_LIST(A, li, m)[i];
+                        pf_v = PC_LIST(A, li, rcp)[i];
+                        pf_gpf = A.trunc ? PC_LIST(A, li, gpf)[i] : 0;
                     }
                 }
             };
@@ -415,10 +433,11 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                                     m32 = A.primes[i];
                                     v = A.primes_rcp[i];
                                 } else {
-                                    info = A.ml.info[i];
-                                    m32 = A.ml.m[i];
-                                    v = A.ml.rcp[i];
-                                    gpf = A.trunc ? A.ml.gpf[i] : 0;
+                                    const u32 li = (fl >> 2) & 7u;
+                                    info = PC_LIST(A, li, info)[i];
+                                    m32 = PC_LIST(A, li, m)[i];
+                                    v = PC_LIST(A, li, rcp)[i];
+                                    gpf = A.trunc ? PC_LIST(A, li, gpf)[i] : 0;
                                 }
                             }
                             one_leaf(info, m32, v, gpf);
@@ -784,6 +803,12 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     A.pit = ctx->T.pi();
     A.rk = ctx->T.rank();
     A.ml = ctx->T.mlist();
+    A.nsl = ctx->T.n_sl;
+    for (int k = 0; k < Tables::NSUB; k++) {
+        A.sl[k] = ctx->T.sublist(k);
+        A.srk[k] = ctx->T.subrank(k);
+        A.slK[k] = k < (int)A.nsl ? ctx->T.sl_K[k] : ~0u;
+    }
     A.primes = ctx->T.primes.as<u32>();
     A.primes_rcp = ctx->T.primes_rcp.as<u64>();
 

@@ -63,6 +63,13 @@ struct Tables {
     u32 ml_cmin = 99;
     u64 ml_n = 0;
     DevBuf ml_m, ml_info, ml_gpf, ml_rcp, rank_bits, rank_cnt;
+    // sub-lists of the m-list: entries with lpf index > sl_K[k] (ascending K), so
+    // that the leaves of a prime p_b with b >= K need not skip entries with lpf <= p_K
+    static constexpr int NSUB = 4;
+    DevBuf sl_m[NSUB], sl_info[NSUB], sl_gpf[NSUB], sl_rcp[NSUB], sl_bits[NSUB], sl_cnt[NSUB];
+    u32 sl_K[NSUB] = {0, 0, 0, 0};
+    u64 sl_n[NSUB] = {0, 0, 0, 0};
+    u32 n_sl = 0;
     // phi(., c) residue tables for the primorial of c (c = 0..7)
     DevBuf phiT[8];
     bool phiT_ok[8] = {false, false, false, false, false, false, false, false};
@@ -73,6 +80,12 @@ struct Tables {
     {
         return MList{ml_m.as<u32>(), ml_info.as<u32>(), ml_gpf.as<u32>(), ml_rcp.as<u64>(), ml_n, ml_limit, ml_cmin};
     }
+    MList sublist(int k) const
+    {
+        return MList{sl_m[k].as<u32>(), sl_info[k].as<u32>(), sl_gpf[k].as<u32>(), sl_rcp[k].as<u64>(), sl_n[k],
+                     ml_limit, sl_K[k]};
+    }
+    RankTable subrank(int k) const { return RankTable{sl_bits[k].as<u64>(), sl_cnt[k].as<u32>(), ml_limit}; }
 };
 
 // ---------------------------------------------------------------- context

@@ -353,6 +353,93 @@ static int build_primes(pc_ctx* ctx, u64 prime_limit)
     return PC_OK;
 }
 
+// ------------------------------------------------------------ sub-lists
+__global__ void sub_flags_kernel(const u32* info, u64 n, u32 K, u32* flags)
+{
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = (info[i] >> 1) > K ? 1u : 0u;
+}
+
+__global__ void sub_scatter_kernel(MList src, const u32* flags, const u32* pos, u32* m, u32* info, u32* gpf, u64* rcp,
+                                   u64* bits)
+{
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= src.n || !flags[i]) return;
+    const u32 j = pos[i];
+    const u32 mi = src.m[i];
+    m[j] = mi;
+    info[j] = src.info[i];
+    gpf[j] = src.gpf[i];
+    rcp[j] = src.rcp[i];
+    atomicOr((unsigned long long*)bits + (mi >> 6), 1ull << (mi & 63));
+}
+
+// The entries of the m-list with lpf index > K, for a few K, each with its own
+// rank table over [0, ml_limit]: the leaves of p_b, b >= K, are read from the
+// largest such list (same order, fewer entries to skip).
+static int build_sublists(pc_ctx* ctx)
+{
+    Tables& T = ctx->T;
+    T.n_sl = 0;
+    static const u32 KS[Tables::NSUB] = {8, 24, 72, 216};
+    const u64 n = T.ml_n, Y = T.ml_limit;
+    if (n == 0) return PC_OK;
+    const u64 nrw = Y / 64 + 1;
+    DevBuf flags, pos, wc;
+    int rc = buf_reserve(ctx, flags, (n + 1) * sizeof(u32));
+    if (rc == PC_OK) rc = buf_reserve(ctx, pos, (n + 1) * sizeof(u32));
+    if (rc == PC_OK) rc = buf_reserve(ctx, wc, (nrw + 1) * sizeof(u32));
+    for (int k = 0; k < Tables::NSUB && rc == PC_OK; k++) {
+        const u32 K = KS[k];
+        if (K <= T.ml_cmin) continue;
+        sub_flags_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(T.ml_info.as<u32>(), n, K, flags.as<u32>());
+        rc = scan_exclusive_u32_to_u32(ctx, flags.as<u32>(), pos.as<u32>(), n);
+        u32 cnt = 0;
+        if (rc == PC_OK) rc = copy_to_host(ctx, &cnt, pos.as<u32>() + n, sizeof(u32));
+        if (rc != PC_OK) break;
+        const int s = T.n_sl;
+        rc = buf_reserve(ctx, T.sl_m[s], ((u64)cnt + 1) * sizeof(u32));
+        if (rc == PC_OK) rc = buf_reserve(ctx, T.sl_info[s], ((u64)cnt + 1) * sizeof(u32));
+        if (rc == PC_OK) rc = buf_reserve(ctx, T.sl_gpf[s], ((u64)cnt + 1) * sizeof(u32));
+        if (rc == PC_OK) rc = buf_reserve(ctx, T.sl_rcp[s], ((u64)cnt + 1) * sizeof(u64));
+        if (rc == PC_OK) rc = buf_reserve(ctx, T.sl_bits[s], nrw * sizeof(u64));
+        if (rc == PC_OK) rc = buf_reserve(ctx, T.sl_cnt[s], (nrw + 1) * sizeof(u32));
+        if (rc != PC_OK) break;
+        cudaError_t e = cudaMemsetAsync(T.sl_bits[s].p, 0, nrw * sizeof(u64), ctx->stream);
+        if (e == cudaSuccess) {
+            sub_scatter_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+                T.mlist(), flags.as<u32>(), pos.as<u32>(), T.sl_m[s].as<u32>(), T.sl_info[s].as<u32>(),
+                T.sl_gpf[s].as<u32>(), T.sl_rcp[s].as<u64>(), T.sl_bits[s].as<u64>());
+            popc_words_kernel<<<(unsigned)((nrw + 255) / 256), 256, 0, ctx->stream>>>(T.sl_bits[s].as<u64>(), nrw,
+                                                                                      wc.as<u32>());
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            pc_set_error(ctx, "m-list sub-lists: %s", cudaGetErrorString(e));
+            rc = PC_ECUDA;
+            break;
+        }
+        rc = scan_exclusive_u32_to_u32(ctx, wc.as<u32>(), T.sl_cnt[s].as<u32>(), nrw);
+        if (rc != PC_OK) break;
+        T.sl_K[s] = K;
+        T.sl_n[s] = cnt;
+        T.n_sl = s + 1;
+        ctx->stats.kernel_launches += 3;
+    }
+    if (rc == PC_OK) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            pc_set_error(ctx, "m-list sub-lists: %s", cudaGetErrorString(e));
+            rc = PC_ECUDA;
+        }
+    }
+    if (rc != PC_OK) T.n_sl = 0;
+    buf_free(flags);
+    buf_free(pos);
+    buf_free(wc);
+    return rc;
+}
+
 static int build_mlist(pc_ctx* ctx, u64 Y, u32 cmin)
 {
     Tables& T = ctx->T;
@@ -453,6 +540,7 @@ int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 
         u32 cm = cmin < T.ml_cmin ? cmin : T.ml_cmin;
         if (T.ml_limit == 0) cm = cmin;
         PC_TRY(build_mlist(ctx, lim, cm));
+        PC_TRY(build_sublists(ctx));
     }
     return PC_OK;
 }
