@@ -149,7 +149,7 @@ int run_trivial(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 // q, consecutive q share the same pi(u).  With l = pi(u), every prime q' >= q
 // with q' <= (x/p_b) / p_l has pi(x/(p_b q')) = l as well (u only falls as q'
 // grows, and stays >= p_l), so the whole run counts (run length) * (l - b + 2)
-// from one division and two pi lookups.  Those leaves (q^2 >= CLUST_K * x/p_b,
+// from two pi lookups and two quotients (p_l is read off the pi record of u).  Those leaves (q^2 >= CLUST_K * x/p_b,
 // i.e. u <= q / CLUST_K) are walked run by run, each thread over a contiguous
 // slice; the rest one leaf per thread.
 static constexpr u32 EASY_CHUNK = 16384;
@@ -238,13 +238,37 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
             const u64 end = pc_min(r.i1, start + per);
             if (start < end) {
                 const u64 qlast = A.primes[end - 1];
+                const float xpf = (float)xp;
                 for (u64 i = start; i < end;) {
                     const u64 u = div_rcp(xp, A.primes[i], A.primes_rcp[i]);
-                    const u64 l = pi_lookup(A.pit, u);
+                    // pi(u) from u's record (u >= p_b >= 13, so 2, 3 and 5 all count),
+                    // and p_l, the largest prime <= u, from the same record when it holds one
+                    const u64 w = u / 240;
+                    const u32 rr = (u32)(u - w * 240);
+                    const u32 e = 8 * (rr / 30) + cntle30(rr % 30);
+                    const uint4 rq = __ldg((const uint4*)(A.pit.rec + w));
+                    const u64 bits = ((u64)rq.x | ((u64)rq.y << 32)) & (e >= 64 ? ~0ull : ((1ull << e) - 1ull));
+                    const u64 l = 3 + rq.z + __popcll(bits);
                     u64 n = 1;
                     if (i + 1 < end) {
-                        // the run: primes q' <= (x/p_b) / p_l
-                        const u64 bound = div_rcp(xp, A.primes[l], A.primes_rcp[l]);
+                        u64 pl;
+                        if (bits) {
+                            const u32 hb = 63 - __clzll((long long)bits);
+                            pl = 240 * w + 30 * (hb >> 3) + r8(hb & 7);
+                        } else {
+                            pl = A.primes[l];
+                        }
+                        // the run: primes q' <= (x/p_b) / p_l.  The quotient is estimated in
+                        // single precision and made exact with integer remainders.
+                        const float rc = __frcp_rn((float)pl);
+                        i64 qb = (i64)(xpf * rc);
+                        i64 rem = (i64)xp - qb * (i64)pl;
+                        const i64 d = (i64)floorf((float)rem * rc);
+                        qb += d;
+                        rem -= d * (i64)pl;
+                        while (rem < 0) { qb--; rem += (i64)pl; }
+                        while (rem >= (i64)pl) { qb++; rem -= (i64)pl; }
+                        const u64 bound = (u64)qb;
                         n = bound >= qlast ? end - i : pi_lookup(A.pit, bound) - i + 1;
                     }
                     s += (i64)n * ((i64)l - (i64)b + 2);
