@@ -156,8 +156,10 @@ int pc_leaf_sums(pc_ctx* ctx, uint64_t x, uint64_t y, uint32_t c, uint64_t a, pc
  * are built once for the whole batch and shared read-only by every query;
  * the queries, largest first, are drained by `streams` slots (pc_params),
  * each a host thread with its own CUDA stream and scratch, so that the
- * kernels of different queries overlap on the GPU.  Every result equals
- * pc_pi_count(x_i, 0).  out is written only if every query succeeded;
+ * kernels of different queries overlap on the GPU.  When at least 64 queries
+ * have x < 2^32, the pi table is extended to the largest of them (at most
+ * 286 MB) and those queries are answered by one lookup kernel.  Every result
+ * equals pc_pi_count(x_i, 0).  out is written only if every query succeeded;
  * otherwise the first failure's code is returned. */
 int pc_pi_count_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint64_t* out, void* stream);
 

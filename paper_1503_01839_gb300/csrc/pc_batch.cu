@@ -229,15 +229,52 @@ extern "C" int pc_pi_count_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint
     } else {
         memcpy(hx.data(), xs, n * sizeof(u64));
     }
-    TableNeeds N;
+    // Queries up to LOOKUP_MAX, if there are enough of them, are answered from
+    // the pi table itself (one lookup kernel for all); the rest run on the slots.
+    static constexpr u64 LOOKUP_MAX = (1ull << 32) - 1;   // the pi table's own limit: 286 MB
+    static constexpr size_t LOOKUP_MIN_QUERIES = 64;
+    u64 lk = 0;
+    size_t nsmall = 0;
     for (size_t i = 0; i < n; i++) {
         if (hx[i] >> 63) return PC_ERANGE;
-        needs_pi(ctx, hx[i], N);
+        if (hx[i] <= LOOKUP_MAX) {
+            lk = pc_max(lk, hx[i]);
+            nsmall++;
+        }
+    }
+    const bool lookup = nsmall >= LOOKUP_MIN_QUERIES;
+    TableNeeds N;
+    if (lookup) N.add(lk, 64, 0, 7);
+    std::vector<Query> q;
+    std::vector<size_t> qi;
+    std::vector<u64> sx;
+    std::vector<size_t> si;
+    for (size_t i = 0; i < n; i++) {
+        if (hx[i] < 2) {
+            hout[i] = 0;   // pi(0) = pi(1) = 0 (the table marks 1 as a wheel residue)
+        } else if (lookup && hx[i] <= LOOKUP_MAX) {
+            sx.push_back(hx[i]);
+            si.push_back(i);
+        } else {
+            needs_pi(ctx, hx[i], N);
+            q.push_back(Query{PC_QUERY_PI, hx[i], 0});
+            qi.push_back(i);
+        }
     }
     PC_TRY(build_needs(ctx, N));
-    std::vector<Query> q(n);
-    for (size_t i = 0; i < n; i++) q[i] = Query{PC_QUERY_PI, hx[i], 0};
-    PC_TRY(run_queries(ctx, q, hout));
+    if (!sx.empty()) {
+        std::vector<u64> sv(sx.size());
+        PC_TRY(tables_pi_many(ctx, sx.data(), sv.data(), sx.size()));
+        for (size_t k = 0; k < sx.size(); k++) hout[si[k]] = sv[k];
+    }
+    if (!q.empty()) {
+        std::vector<u64> qv(q.size(), 0);
+        PC_TRY(run_queries(ctx, q, qv));   // sets the batch's counters
+        for (size_t k = 0; k < q.size(); k++) hout[qi[k]] = qv[k];
+    } else {
+        memset(&ctx->stats, 0, sizeof(ctx->stats));
+    }
+    if (!sx.empty()) ctx->stats.kernel_launches++;
     if (stream) {
         PC_CUDA(ctx, cudaMemcpyAsync(out, hout.data(), n * sizeof(u64), cudaMemcpyHostToDevice, (cudaStream_t)stream));
         PC_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));

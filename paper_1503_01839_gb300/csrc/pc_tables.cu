@@ -518,10 +518,18 @@ int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 
     }
     PC_TRY(ensure_small(ctx));
     bool new_pi = false;
+    // The table is sieved with the bootstrap primes <= 65536, which suffice up to
+    // 65536^2 = 2^32 (every query x < 2^63 needs at most isqrt(x) < 3.04e9).
+    static constexpr u64 PI_TABLE_MAX = (1ull << 32) - 1;
+    if (pi_limit > PI_TABLE_MAX) {
+        pc_set_error(ctx, "pi table limited to 2^32 - 1 (asked for %llu)", (unsigned long long)pi_limit);
+        return PC_EINVAL;
+    }
     if (pi_limit > T.pi_limit) {
         // grow geometrically so that a rising sequence of queries rebuilds rarely
         u64 lim = pi_limit;
         if (T.pi_limit && lim < T.pi_limit + T.pi_limit / 2) lim = T.pi_limit + T.pi_limit / 2;
+        if (lim > PI_TABLE_MAX) lim = PI_TABLE_MAX;
         PC_TRY(build_pi(ctx, lim));
         new_pi = true;
     }

@@ -203,3 +203,13 @@ def test_batch_after_autotune_over_many_decades(alone):
         cx.autotune(min(xs), max(xs), reps=1)
         got = cx.pi_count_batch(xs)
     assert got == [alone.pi_count(x) for x in xs]
+
+
+def test_batch_small_queries_from_the_table(alone, pi_pow2):
+    # at least 64 queries < 2^32 are answered by table lookups; mixed with larger ones
+    xs = inputs.log_uniform_x(120, 8.0, 9.6, seed=51) + [1 << 31, (1 << 32) - 1, 1 << 32, 10 ** 12]
+    with pc.Context(0, streams=4) as cx:
+        got = cx.pi_count_batch(xs)
+    assert got == [alone.pi_count(x) for x in xs]
+    assert got[-4] == pi_pow2[31]          # Table 2, answered by the lookup
+    assert got[-2] == pi_pow2[32]          # Table 2, just beyond the lookup range
