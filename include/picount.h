@@ -66,7 +66,11 @@ typedef struct pc_params {
     uint32_t streams;     /* concurrent query slots of pc_pi_count_batch and of
                              the server (1..64): each slot is one host thread
                              with its own CUDA stream and scratch; default 8 */
-    uint32_t reserved;
+    uint32_t pi_gather;   /* how the easy leaves read pi(u): 0 = the popcount pi
+                             table (one 16-byte record per 240 integers, the
+                             default); 1 = the sampled table of Section 2.1
+                             (pi at every floor(log2 y)-th integer, then a walk
+                             along the primes) */
 } pc_params;
 
 /* Counters and phase times of the last successful call. */

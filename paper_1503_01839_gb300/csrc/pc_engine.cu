@@ -45,7 +45,7 @@ extern "C" int pc_create(pc_ctx** out, int device, const pc_params* p)
     const uint32_t wb = ctx->params.warp_bytes;
     if (ctx->params.c > 7 || (sb && sb != 1024 && sb != 2048 && (sb % 4096 || sb > 131072)) ||
         (wb && wb != 1024 && wb != 2048 && wb != 4096 && wb != 8192) ||
-        ctx->params.ctas_per_sm > 4 ||
+        ctx->params.ctas_per_sm > 4 || ctx->params.pi_gather > 1 ||
         (ctx->params.threads && (ctx->params.threads % 32 || ctx->params.threads < 128 || ctx->params.threads > 1024))) {
         delete ctx;
         return PC_EINVAL;
@@ -84,7 +84,7 @@ extern "C" void pc_destroy(pc_ctx* ctx)
     if (!ctx->borrowed) {
         Tables& T = ctx->T;
         DevBuf* tabs[] = {&T.small_primes, &T.pi_rec, &T.primes, &T.primes_rcp, &T.ml_m, &T.ml_info,
-                          &T.ml_gpf, &T.ml_rcp, &T.rank_bits, &T.rank_cnt};
+                          &T.ml_gpf, &T.ml_rcp, &T.rank_bits, &T.rank_cnt, &T.samp};
         for (DevBuf* b : tabs) buf_free(*b);
         for (int c = 0; c < 8; c++) buf_free(T.phiT[c]);
         for (int k = 0; k < Tables::NSUB; k++) {

@@ -70,6 +70,10 @@ struct Tables {
     u32 sl_K[NSUB] = {0, 0, 0, 0};
     u64 sl_n[NSUB] = {0, 0, 0, 0};
     u32 n_sl = 0;
+    // sampled pi table (Section 2.1): samp[j] = pi(j * samp_s), covering every v <= samp_limit
+    DevBuf samp;
+    u32 samp_s = 0;
+    u64 samp_limit = 0;
     // phi(., c) residue tables for the primorial of c (c = 0..7)
     DevBuf phiT[8];
     bool phiT_ok[8] = {false, false, false, false, false, false, false, false};

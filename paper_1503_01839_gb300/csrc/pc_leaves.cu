@@ -25,7 +25,26 @@ struct LeafArgs {
     const u32* primes;
     const u64* primes_rcp;   // floor((2^64 - 1) / p_k)
     u64 n_lim;   // list entries with m <= y: [0, n_lim)
+    // easy-leaf gathers from the sampled table of Section 2.1 instead of the pi table
+    const u32* samp;
+    u32 samp_s;
+    u32 sampled;
 };
+
+// pi(v) and p_pi(v) from the sampled table: start at pi(floor(v/s) * s), then
+// step along the primes while the next one is <= v (on average about
+// s / ln v < 1 step; the prime table ends with a sentinel prime above every v).
+__device__ __forceinline__ u64 pi_sampled(const LeafArgs& A, u64 v, u64* pv)
+{
+    u64 k = A.samp[v / A.samp_s];
+    u64 nxt = A.primes[k + 1];
+    while (nxt <= v) {
+        k++;
+        nxt = A.primes[k + 1];
+    }
+    *pv = A.primes[k];
+    return k;
+}
 
 static LeafArgs make_args(pc_ctx* ctx, const LeafProblem& P, u64 n_lim)
 {
@@ -41,6 +60,9 @@ static LeafArgs make_args(pc_ctx* ctx, const LeafProblem& P, u64 n_lim)
     A.primes = ctx->T.primes.as<u32>();
     A.primes_rcp = ctx->T.primes_rcp.as<u64>();
     A.n_lim = n_lim;
+    A.samp = ctx->T.samp.as<u32>();
+    A.samp_s = ctx->T.samp_s;
+    A.sampled = ctx->params.pi_gather == 1;
     return A;
 }
 
@@ -241,23 +263,27 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
                 const float xpf = (float)xp;
                 for (u64 i = start; i < end;) {
                     const u64 u = div_rcp(xp, A.primes[i], A.primes_rcp[i]);
-                    // pi(u) from u's record (u >= p_b >= 13, so 2, 3 and 5 all count),
-                    // and p_l, the largest prime <= u, from the same record when it holds one
-                    const u64 w = u / 240;
-                    const u32 rr = (u32)(u - w * 240);
-                    const u32 e = 8 * (rr / 30) + cntle30(rr % 30);
-                    const uint4 rq = __ldg((const uint4*)(A.pit.rec + w));
-                    const u64 bits = ((u64)rq.x | ((u64)rq.y << 32)) & (e >= 64 ? ~0ull : ((1ull << e) - 1ull));
-                    const u64 l = 3 + rq.z + __popcll(bits);
-                    u64 n = 1;
-                    if (i + 1 < end) {
-                        u64 pl;
+                    u64 l, pl;
+                    if (A.sampled) {
+                        l = pi_sampled(A, u, &pl);
+                    } else {
+                        // pi(u) from u's record (u >= p_b >= 13, so 2, 3 and 5 all count),
+                        // and p_l, the largest prime <= u, from the same record when it holds one
+                        const u64 w = u / 240;
+                        const u32 rr = (u32)(u - w * 240);
+                        const u32 e = 8 * (rr / 30) + cntle30(rr % 30);
+                        const uint4 rq = __ldg((const uint4*)(A.pit.rec + w));
+                        const u64 bits = ((u64)rq.x | ((u64)rq.y << 32)) & (e >= 64 ? ~0ull : ((1ull << e) - 1ull));
+                        l = 3 + rq.z + __popcll(bits);
+                        pl = 0;
                         if (bits) {
                             const u32 hb = 63 - __clzll((long long)bits);
                             pl = 240 * w + 30 * (hb >> 3) + r8(hb & 7);
-                        } else {
-                            pl = A.primes[l];
                         }
+                    }
+                    u64 n = 1;
+                    if (i + 1 < end) {
+                        if (pl == 0) pl = A.primes[l];
                         // the run: primes q' <= (x/p_b) / p_l.  The quotient is estimated in
                         // single precision and made exact with integer remainders.
                         const float rc = __frcp_rn((float)pl);
@@ -269,7 +295,9 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
                         while (rem < 0) { qb--; rem += (i64)pl; }
                         while (rem >= (i64)pl) { qb++; rem -= (i64)pl; }
                         const u64 bound = (u64)qb;
-                        n = bound >= qlast ? end - i : pi_lookup(A.pit, bound) - i + 1;
+                        u64 pb;
+                        n = bound >= qlast ? end - i
+                                           : (A.sampled ? pi_sampled(A, bound, &pb) : pi_lookup(A.pit, bound)) - i + 1;
                     }
                     s += (i64)n * ((i64)l - (i64)b + 2);
                     i += n;
@@ -295,14 +323,21 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
             }
             // easy: p_b <= u < y < 2^32; for b > 3, u >= 7 and pi(u) counts 2, 3, 5
             const u32 u = (u32)div_rcp(xp, m, v);
-            const u32 w = u / 240, rr = u - w * 240;
-            const u32 e = 8 * (rr / 30) + cntle30(rr % 30);   // 0..64
-            const uint4 q = __ldg((const uint4*)(A.pit.rec + w));
-            u32 c;
-            if (e <= 32) c = __popc(q.x & (e == 32 ? ~0u : (1u << e) - 1u));
-            else c = __popc(q.x) + __popc(q.y & (e == 64 ? ~0u : (1u << (e - 32)) - 1u));
-            const u32 small = b > 3 ? 3u : (u >= 2) + (u >= 3) + (u >= 5);
-            const i64 t2 = (i64)(small + q.z + c) - (i64)b + 2;
+            u64 piu;
+            if (A.sampled) {
+                u64 pv;
+                piu = pi_sampled(A, u, &pv);
+            } else {
+                const u32 w = u / 240, rr = u - w * 240;
+                const u32 e = 8 * (rr / 30) + cntle30(rr % 30);   // 0..64
+                const uint4 q = __ldg((const uint4*)(A.pit.rec + w));
+                u32 c;
+                if (e <= 32) c = __popc(q.x & (e == 32 ? ~0u : (1u << e) - 1u));
+                else c = __popc(q.x) + __popc(q.y & (e == 64 ? ~0u : (1u << (e - 32)) - 1u));
+                const u32 small = b > 3 ? 3u : (u >= 2) + (u >= 3) + (u >= 5);
+                piu = small + q.z + c;
+            }
+            const i64 t2 = (i64)piu - (i64)b + 2;
             s += neg ? t2 : -t2;
         }
     }

@@ -353,6 +353,31 @@ static int build_primes(pc_ctx* ctx, u64 prime_limit)
     return PC_OK;
 }
 
+// ------------------------------------------------------ sampled pi table
+__global__ void sampled_kernel(PiTable pit, u64 n, u32 step, u32* samp)
+{
+    const u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) samp[j] = (u32)pi_lookup(pit, j * step);
+}
+
+// pi at every step-th integer up to limit, step = floor(log2 limit) (Section 2.1).
+static int build_sampled(pc_ctx* ctx, u64 limit)
+{
+    Tables& T = ctx->T;
+    u32 step = 0;
+    for (u64 v = limit; v > 1; v >>= 1) step++;   // floor(log2 limit)
+    if (step < 1) step = 1;
+    const u64 n = limit / step + 1;
+    PC_TRY(buf_reserve(ctx, T.samp, n * sizeof(u32)));
+    sampled_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(T.pi(), n, step, T.samp.as<u32>());
+    PC_LAUNCHED(ctx);
+    PC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->stats.kernel_launches++;
+    T.samp_s = step;
+    T.samp_limit = limit;   // every v <= limit has v / step < n
+    return PC_OK;
+}
+
 // ------------------------------------------------------------ sub-lists
 __global__ void sub_flags_kernel(const u32* info, u64 n, u32 K, u32* flags)
 {
@@ -511,7 +536,8 @@ int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 
     if (ctx->borrowed) {
         // a worker reads its parent's tables and must find them big enough
         if (T.n_small && pi_limit <= T.pi_limit && prime_limit <= T.prime_limit &&
-            (ml_limit == 0 || (ml_limit <= T.ml_limit && cmin >= T.ml_cmin)))
+            (ml_limit == 0 || (ml_limit <= T.ml_limit && cmin >= T.ml_cmin &&
+                               (ctx->params.pi_gather == 0 || ml_limit <= T.samp_limit))))
             return PC_OK;
         pc_set_error(ctx, "query needs tables beyond those prepared for the batch");
         return PC_EINVAL;
@@ -550,6 +576,9 @@ int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 
         PC_TRY(build_mlist(ctx, lim, cm));
         PC_TRY(build_sublists(ctx));
     }
+    // the sampled table serves the easy leaves, whose u stays below the m-list limit y
+    if (ctx->params.pi_gather == 1 && ml_limit > 0 && T.ml_limit > T.samp_limit)
+        PC_TRY(build_sampled(ctx, T.ml_limit));
     return PC_OK;
 }
 

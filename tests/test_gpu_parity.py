@@ -222,3 +222,21 @@ def test_largest_x_is_consistent():
         assert cx.pi_count(x, 30) == v
     with pc.Context(0) as cx:
         assert cx.pi_count(1 << 62, 0) < v
+
+
+@pytest.mark.parametrize("x,alpha", [(10 ** 9, 5), (10 ** 11, 2), (10 ** 12, 6), (2 ** 35, 3)])
+def test_sampled_pi_table_parity(x, alpha):
+    # easy leaves reading pi(u) from the sampled table of Section 2.1 instead of the popcount table
+    y = y_for(x, alpha)
+    with pc.Context(0, pi_gather=1) as cx:
+        for c in (0, 3, 5):
+            want = o.leaf_sums(x, y, c)
+            got = cx.leaf_sums(x, y, c)
+            for k in ("S1", "S2_triv", "S2_easy", "S2_hard", "P2"):
+                assert got[k] == want[k], (x, y, c, k, got[k], want[k])
+
+
+def test_sampled_pi_table_full_size(pi_pow10):
+    with pc.Context(0, pi_gather=1) as cx:
+        assert cx.pi_count(10 ** 16) == pi_pow10[16]
+        assert cx.pi_count(10 ** 18, 48) == pi_pow10[18]
