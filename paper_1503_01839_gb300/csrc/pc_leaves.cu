@@ -233,6 +233,9 @@ __global__ void easy_chunk_map_kernel(u64 nb, const u64* choff, u32* cmap)
     for (u64 ch = choff[t]; ch < choff[t + 1]; ch++) cmap[ch] = (u32)t;
 }
 
+// SAMPLED: read pi(u) from the sampled table instead of the popcount table
+// (a template parameter, so that the default instantiation carries no trace of it)
+template <bool SAMPLED>
 __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u64* choff, const u32* cmap,
                             u64 nchunks, unsigned long long* queue, I128Pair* part)
 {
@@ -263,27 +266,29 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
                 const float xpf = (float)xp;
                 for (u64 i = start; i < end;) {
                     const u64 u = div_rcp(xp, A.primes[i], A.primes_rcp[i]);
-                    u64 l, pl;
-                    if (A.sampled) {
+                    u64 l, pl = 0, w = 0, bits = 0;
+                    if (SAMPLED) {
                         l = pi_sampled(A, u, &pl);
                     } else {
-                        // pi(u) from u's record (u >= p_b >= 13, so 2, 3 and 5 all count),
-                        // and p_l, the largest prime <= u, from the same record when it holds one
-                        const u64 w = u / 240;
+                        // pi(u) from u's record (u >= p_b >= 13, so 2, 3 and 5 all count)
+                        w = u / 240;
                         const u32 rr = (u32)(u - w * 240);
                         const u32 e = 8 * (rr / 30) + cntle30(rr % 30);
                         const uint4 rq = __ldg((const uint4*)(A.pit.rec + w));
-                        const u64 bits = ((u64)rq.x | ((u64)rq.y << 32)) & (e >= 64 ? ~0ull : ((1ull << e) - 1ull));
+                        bits = ((u64)rq.x | ((u64)rq.y << 32)) & (e >= 64 ? ~0ull : ((1ull << e) - 1ull));
                         l = 3 + rq.z + __popcll(bits);
-                        pl = 0;
-                        if (bits) {
-                            const u32 hb = 63 - __clzll((long long)bits);
-                            pl = 240 * w + 30 * (hb >> 3) + r8(hb & 7);
-                        }
                     }
                     u64 n = 1;
                     if (i + 1 < end) {
-                        if (pl == 0) pl = A.primes[l];
+                        if (!SAMPLED) {
+                            // p_l, the largest prime <= u, from the same record when it holds one
+                            if (bits) {
+                                const u32 hb = 63 - __clzll((long long)bits);
+                                pl = 240 * w + 30 * (hb >> 3) + r8(hb & 7);
+                            } else {
+                                pl = A.primes[l];
+                            }
+                        }
                         // the run: primes q' <= (x/p_b) / p_l.  The quotient is estimated in
                         // single precision and made exact with integer remainders.
                         const float rc = __frcp_rn((float)pl);
@@ -297,7 +302,7 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
                         const u64 bound = (u64)qb;
                         u64 pb;
                         n = bound >= qlast ? end - i
-                                           : (A.sampled ? pi_sampled(A, bound, &pb) : pi_lookup(A.pit, bound)) - i + 1;
+                                           : (SAMPLED ? pi_sampled(A, bound, &pb) : pi_lookup(A.pit, bound)) - i + 1;
                     }
                     s += (i64)n * ((i64)l - (i64)b + 2);
                     i += n;
@@ -324,7 +329,7 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
             // easy: p_b <= u < y < 2^32; for b > 3, u >= 7 and pi(u) counts 2, 3, 5
             const u32 u = (u32)div_rcp(xp, m, v);
             u64 piu;
-            if (A.sampled) {
+            if (SAMPLED) {
                 u64 pv;
                 piu = pi_sampled(A, u, &pv);
             } else {
@@ -376,7 +381,11 @@ int run_easy(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     PC_TRY(buf_reserve(ctx, ctx->partials, g * sizeof(I128Pair)));
     PC_TRY(buf_reserve(ctx, ctx->queue, 64));
     PC_CUDA(ctx, cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream));
-    easy_kernel<<<g, 256, 0, ctx->stream>>>(A, b_lo, ctx->easy_rng.as<EasyRange>(), choff, ctx->easy_cmap.as<u32>(), nchunks,
+    if (A.sampled)
+        easy_kernel<true><<<g, 256, 0, ctx->stream>>>(A, b_lo, ctx->easy_rng.as<EasyRange>(), choff, ctx->easy_cmap.as<u32>(), nchunks,
+                                            (unsigned long long*)ctx->queue.p, ctx->partials.as<I128Pair>());
+    else
+        easy_kernel<false><<<g, 256, 0, ctx->stream>>>(A, b_lo, ctx->easy_rng.as<EasyRange>(), choff, ctx->easy_cmap.as<u32>(), nchunks,
                                             (unsigned long long*)ctx->queue.p, ctx->partials.as<I128Pair>());
     PC_LAUNCHED(ctx);
     ctx->stats.kernel_launches++;
