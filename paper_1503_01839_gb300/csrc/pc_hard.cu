@@ -42,6 +42,8 @@
 
 static constexpr u32 BATCH = 64;
 static constexpr u32 RECOUNT_P = 128;   // below this a warp recounts its blocks after crossing off
+static constexpr u32 GROUP_P = 128;     // smallest prime crossed off in groups of leaf-free steps
+static_assert(GROUP_P >= RECOUNT_P, "grouped steps keep their block counters up to date");
 static constexpr u32 MAX_NW = 16;       // warps (sub-ranges) per segment
 static constexpr u32 MAX_SUB = 8192;    // bytes per sub-range: up to 256 blocks of 256 bits
 static constexpr u32 MAX_SEG = 131072;  // bytes per segment
@@ -99,7 +101,8 @@ struct __align__(16) StepInfo {
     u32 r0;        // L mod p_b
     u32 coff[8];   // floor(p * R8[j] / 30): byte offset of class j inside a wheel round
     u8 cbit[8];    // bit of class j inside its byte
-    u32 flags;     // bit 0: leaves are primes, bit 1: step has leaves, bits 2-4: m-list (0 = all, k = sub-list k-1)
+    u32 flags;     // bit 0: leaves are primes, bit 1: step has leaves, bits 2-4: m-list (0 = all, k = sub-list k-1),
+                   // bit 5: p >= GROUP_P and p^3 > the last integer of the segment (see group_cross)
     u32 pself;     // segment bit of p_b itself, or ~0
     u32 row;       // off[b - k0]: start of the count / tally rows of b
     u32 pad[3];
@@ -229,6 +232,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         if (A.slK[k] <= b) li = k + 1;
                     si.flags = 2u | (p * p > A.y ? 1u : 0u) | (li << 2);
                 }
+                if (p >= GROUP_P && p * p > div_rcp(L + A.span - 1, p, vp)) si.flags |= 32u;
                 for (int j = 0; j < 8; j++) {
                     const u32 pr = (u32)p * r8(j);
                     si.coff[j] = pr / 30;
@@ -296,18 +300,19 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                     j1 = a1;
                 }
             };
-            u64 busy = 0, leafy = 0;
+            u64 busy = 0, leafy = 0, grp = 0;
             u32 lj0[BATCH / 32], lj1[BATCH / 32];   // leaf range of step h*32 + lane
 #pragma unroll
             for (u32 h = 0; h < BATCH / 32; h++) {
                 const u32 t = h * 32 + lane;
-                bool on = false;
+                bool on = false, g = false;
                 lj0[h] = lj1[h] = 0;
                 if (t < nb) {
                     const u32 b = bb + t, fl = st[t].flags, ps = st[t].pself;
                     if (b < Bs) {
                         if (basew[t * nw + w] < (i32)sub_bytes) on = true;
                         if (ps != ~0u && (ps >> A.sub_shift) == w) on = true;
+                        g = (fl & 32u) != 0;
                     }
                     if (b > A.kleaf && (fl & 2u)) {
                         leaf_range(t, lj0[h], lj1[h]);
@@ -317,7 +322,9 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 }
                 busy |= (u64)__ballot_sync(0xffffffffu, on) << (h * 32);
                 leafy |= (u64)__ballot_sync(0xffffffffu, lj1[h] > lj0[h]) << (h * 32);
+                grp |= (u64)__ballot_sync(0xffffffffu, g) << (h * 32);
             }
+            grp &= busy & ~leafy;
             // Leaf data (m, its reciprocal, lpf index and mu) does not depend on the
             // sieve, so the first 32 leaves of the next leaf step are loaded ahead,
             // while the warp is still crossing off earlier primes.
@@ -352,9 +359,78 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
             nleafy += __popcll(leafy);
             if (leafy) prefetch(__ffsll((long long)leafy) - 1);
             __syncwarp();
+            // A run of consecutive busy steps without leaves in this sub-range, all of
+            // primes p with p >= GROUP_P and p^3 > every integer of the segment, is
+            // crossed off in one go: lane = (step of the run, residue class j), four
+            // steps per pass.  A bit still set here is 1, a prime, or a product of primes
+            // that are all >= the run's first prime; below that prime cubed it has at
+            // most two of them, so exactly one lane of the run reaches it: the one of its
+            // least prime factor q, at the cofactor n / q >= q.  That lane's decrement is
+            // therefore the one the steps would make in order, and the per-step counts
+            // follow by a prefix sum.  Lanes of different primes may share a word, hence
+            // the atomics.
+            auto group_cross = [&](u64 run) {
+                const u32 nr = __popcll(run), lo32 = (u32)run, hi32 = (u32)(run >> 32), nlo = __popc(lo32);
+                const u32 slot = lane >> 3, j = lane & 7;
+                for (u32 c = 0; c < nr; c += 4) {
+                    const u32 n = c + slot;
+                    u32 d = 0, tt = 0;
+                    if (n < nr) {
+                        tt = n < nlo ? __fns(lo32, 0, (int)n + 1) : 32 + __fns(hi32, 0, (int)(n - nlo) + 1);
+                        const i32 p = (i32)st[tt].p;
+                        const u32 kmod = kmodw[tt * nw + w];
+                        const u32 bj = st[tt].cbit[j];
+                        i32 by = basew[tt * nw + w] + (i32)st[tt].coff[j] + (r8(j) < kmod ? p : 0);
+                        for (; by < (i32)sub_bytes; by += p) {
+                            const u32 pos = ((u32)by << 3) + bj, mask = 1u << (pos & 31);
+                            if (atomicAnd(&my[pos >> 5], ~mask) & mask) {
+                                d++;
+                                atomicSub(&myblk32[pos >> 9], 1u << (16 * ((pos >> 8) & 1)));
+                            }
+                            nclears++;
+                        }
+                        const u32 ps = st[tt].pself;
+                        if (j == 0 && ps != ~0u && (ps >> A.sub_shift) == w) {   // p itself
+                            const u32 pos = ps & (sub_bits - 1), mask = 1u << (pos & 31);
+                            if (atomicAnd(&my[pos >> 5], ~mask) & mask) {
+                                d++;
+                                atomicSub(&myblk32[pos >> 9], 1u << (16 * ((pos >> 8) & 1)));
+                            }
+                        }
+                    }
+                    d += __shfl_xor_sync(0xffffffffu, d, 1);
+                    d += __shfl_xor_sync(0xffffffffu, d, 2);
+                    d += __shfl_xor_sync(0xffffffffu, d, 4);
+                    if (j == 0 && n < nr) cw[tt * nw + w] = d;   // decrement of step tt for now
+                }
+                __syncwarp();
+#pragma unroll
+                for (u32 h = 0; h < BATCH / 32; h++) {   // counts after every step of the run, in order
+                    const u32 t2 = h * 32 + lane;
+                    const bool in = (run >> t2) & 1u;
+                    const u32 v = in ? cw[t2 * nw + w] : 0u;
+                    u32 incl = v;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const u32 up = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += up;
+                    }
+                    if (in) cw[t2 * nw + w] = cnt - incl;
+                    cnt -= __shfl_sync(0xffffffffu, incl, 31);
+                }
+                __syncwarp();
+            };
             const u32 cnt0 = cnt;
-            for (u64 todo = busy; todo; todo &= todo - 1) {
+            for (u64 todo = busy; todo;) {
                 const u32 t = __ffsll((long long)todo) - 1;
+                if ((grp >> t) & 1u) {
+                    // the run ends below the next busy step that is not in grp
+                    const u64 stop = busy & ~grp & (~0ull << t);
+                    const u64 run = grp & (~0ull << t) & (stop ? (stop & (0ull - stop)) - 1 : ~0ull);
+                    group_cross(run);
+                    todo &= ~run;
+                    continue;
+                }
+                todo &= todo - 1;
                 const u32 b = bb + t;
                 const u32 fl = st[t].flags;
                 if (b > A.kleaf) {
