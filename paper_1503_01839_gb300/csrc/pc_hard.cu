@@ -482,16 +482,20 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                             u32 bi = e >> 8;
                             if (bi >= nbw) bi = nbw - 1;
                             // set bits of block bi below the end (0..256 of them): both halves
-                            // of the block at once, every word masked, no data-dependent loop
+                            // of the block at once, no data-dependent loop.  Word i keeps its
+                            // bits below rem - 64 i by a left shift of 64 (i + 1) - rem, taken
+                            // as at least 0; PTX clamps a 64-bit shift above 64 to 64 (result 0).
                             const u32 rem = e - (bi << 8);
                             const ulonglong2 h0 = ((const ulonglong2*)my64)[2 * bi];
                             const ulonglong2 h1 = ((const ulonglong2*)my64)[2 * bi + 1];
-                            auto part = [&](u64 wv, u32 lo) -> u32 {
-                                const u32 sh = rem <= lo ? 0u : (rem - lo >= 64 ? 64u : rem - lo);
-                                const u64 mk = sh >= 64 ? ~0ull : ((1ull << sh) - 1ull);
-                                return __popcll(wv & mk);
+                            auto part = [&](u64 wv, u32 i) -> u32 {
+                                i32 sh = (i32)(64 * i + 64) - (i32)rem;
+                                sh = sh < 0 ? 0 : (sh > 64 ? 64 : sh);
+                                u64 r;
+                                asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(wv), "r"(sh));
+                                return __popcll(r);
                             };
-                            const u32 c = mypre[bi] + part(h0.x, 0) + part(h0.y, 64) + part(h1.x, 128) + part(h1.y, 192);
+                            const u32 c = mypre[bi] + part(h0.x, 0) + part(h0.y, 1) + part(h1.x, 2) + part(h1.y, 3);
                             acc += neg ? (i64)c : -(i64)c;
                             tl += neg ? 1 : -1;
                             nleaves++;
