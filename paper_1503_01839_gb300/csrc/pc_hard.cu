@@ -432,7 +432,12 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 }
                 todo &= todo - 1;
                 const u32 b = bb + t;
-                const u32 fl = st[t].flags;
+                // the step's data, all loaded at once rather than as a chain of loads
+                const u32 fl = st[t].flags, p = st[t].p, ps = st[t].pself;
+                const i32 base = basew[t * nw + w];
+                const u32 kmod = kmodw[t * nw + w];
+                const i32 cj = (i32)st[t].coff[lane & 7];
+                const u32 bj = st[t].cbit[lane & 7];
                 if (b > A.kleaf) {
                     int tl = 0;
                     if ((leafy >> t) & 1u) {
@@ -527,7 +532,6 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                     }
                 }
                 if (b < Bs) {
-                    const u32 p = st[t].p;
                     const bool recount = p < RECOUNT_P;
                     u32 dec = 0;
                     auto clear_bit = [&](u32 pos) {   // pos: bit inside this warp's sub-range
@@ -540,17 +544,12 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         }
                     };
                     {
-                        const i32 base = basew[t * nw + w];
                         if (base < (i32)sub_bytes) {
-                            const u32 kmod = kmodw[t * nw + w];
-                            const uint2 bv = *(const uint2*)st[t].cbit;
                             if (p >= 128) {
                                 // lane = (class j, round offset o): four rounds per pass.
                                 // Two crossings of one prime p >= 128 by different lanes
                                 // are >= 4 bytes apart, so no two lanes share a word.
                                 const u32 j = lane & 7, o = lane >> 3;
-                                const i32 cj = (i32)st[t].coff[j];
-                                const u32 bj = ((j < 4 ? bv.x : bv.y) >> (8 * (j & 3))) & 0xFFu;
                                 // round o, or o + 4 when round 0 starts below the first cofactor;
                                 // every byte reached from there is >= 0 (k >= klo)
                                 const i32 step4 = 4 * (i32)p;
@@ -580,6 +579,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                                 }
                                 nclears += n;
                             } else {
+                                const uint2 bv = *(const uint2*)st[t].cbit;
                                 const uint4 c0 = *(const uint4*)st[t].coff, c1 = *(const uint4*)(st[t].coff + 4);
                                 const u32 cw8[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
                                 // lane = whole wheel rounds, even rounds first, then odd ones.
@@ -612,7 +612,6 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         }
                     }
                     __syncwarp();
-                    const u32 ps = st[t].pself;
                     if (lane == 0 && ps != ~0u && (ps >> A.sub_shift) == w) clear_bit(ps & (sub_bits - 1));
                     if (recount) {
                         __syncwarp();
