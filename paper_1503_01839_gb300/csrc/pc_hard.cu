@@ -398,23 +398,14 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                             }
                         }
                     }
-                    d += __shfl_xor_sync(0xffffffffu, d, 1);
-                    d += __shfl_xor_sync(0xffffffffu, d, 2);
-                    d += __shfl_xor_sync(0xffffffffu, d, 4);
-                    if (j == 0 && n < nr) cw[tt * nw + w] = d;   // decrement of step tt for now
-                }
-                __syncwarp();
-#pragma unroll
-                for (u32 h = 0; h < BATCH / 32; h++) {   // counts after every step of the run, in order
-                    const u32 t2 = h * 32 + lane;
-                    const bool in = (run >> t2) & 1u;
-                    const u32 v = in ? cw[t2 * nw + w] : 0u;
-                    u32 incl = v;
+                    // lanes 8s .. 8s+7 hold step c+s: an inclusive scan over the warp gives,
+                    // at lane 8s+7, the decrement of the steps up to c+s
+                    u32 incl = d;
                     for (int o = 1; o < 32; o <<= 1) {
                         const u32 up = __shfl_up_sync(0xffffffffu, incl, o);
                         if (lane >= o) incl += up;
                     }
-                    if (in) cw[t2 * nw + w] = cnt - incl;
+                    if (j == 7 && n < nr) cw[tt * nw + w] = cnt - incl;
                     cnt -= __shfl_sync(0xffffffffu, incl, 31);
                 }
                 __syncwarp();
