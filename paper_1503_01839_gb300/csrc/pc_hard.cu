@@ -88,10 +88,6 @@ struct HardArgs {
     unsigned long long* stat;      // [0] hard leaves, [1] multiples crossed off
 };
 
-// field f of the m-list a step reads its leaves from (li from its flags)
-#define PC_LIST(A, li, f)                                                                                      \
-    ((li) == 0 ? (A).ml.f : (li) == 1 ? (A).sl[0].f : (li) == 2 ? (A).sl[1].f : (li) == 3 ? (A).sl[2].f : (A).sl[3].f)
-
 struct __align__(16) StepInfo {
     u64 xp;        // x / p_b
     u64 q;         // L / p_b
@@ -152,9 +148,21 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
     __shared__ u64 rLk[MAX_NW + 1];   // reciprocals of L + k * dspan, k = 0..nw
     __shared__ u32 s_item;
     __shared__ i128 red[32];
+    // the m-lists a step may read its leaves from: index 0 the whole list, k the sub-list k-1
+    __shared__ const u32* lst_info[1 + Tables::NSUB];
+    __shared__ const u32* lst_m[1 + Tables::NSUB];
+    __shared__ const u32* lst_gpf[1 + Tables::NSUB];
+    __shared__ const u64* lst_rcp[1 + Tables::NSUB];
 
     const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5, NT = blockDim.x;
     make_pattern_words(patw, A.k0);
+    if (tid <= Tables::NSUB) {
+        const MList& l = tid == 0 ? A.ml : A.sl[tid - 1];
+        lst_info[tid] = l.info;
+        lst_m[tid] = l.m;
+        lst_gpf[tid] = l.gpf;
+        lst_rcp[tid] = l.rcp;
+    }
     u32* my = bits + w * sub_words;
     const u64* my64 = (const u64*)my;
     u16* myblk = blk + w * nbw;
@@ -348,10 +356,10 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         pf_gpf = 0;
                     } else {
                         const u32 li = (st[t].flags >> 2) & 7u;
-                        pf_info = PC_LIST(A, li, info)[i];
-                        pf_m = PC_LIST(A, li, m)[i];
-                        pf_v = PC_LIST(A, li, rcp)[i];
-                        pf_gpf = A.trunc ? PC_LIST(A, li, gpf)[i] : 0;
+                        pf_info = lst_info[li][i];
+                        pf_m = lst_m[li][i];
+                        pf_v = lst_rcp[li][i];
+                        pf_gpf = A.trunc ? lst_gpf[li][i] : 0;
                     }
                 }
             };
@@ -510,10 +518,10 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                                     v = A.primes_rcp[i];
                                 } else {
                                     const u32 li = (fl >> 2) & 7u;
-                                    info = PC_LIST(A, li, info)[i];
-                                    m32 = PC_LIST(A, li, m)[i];
-                                    v = PC_LIST(A, li, rcp)[i];
-                                    gpf = A.trunc ? PC_LIST(A, li, gpf)[i] : 0;
+                                    info = lst_info[li][i];
+                                    m32 = lst_m[li][i];
+                                    v = lst_rcp[li][i];
+                                    gpf = A.trunc ? lst_gpf[li][i] : 0;
                                 }
                             }
                             one_leaf(info, m32, v, gpf);
