@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
     __shared__ const u32* lst_m[1 + Tables::NSUB];
     __shared__ const u32* lst_gpf[1 + Tables::NSUB];
     __shared__ const u64* lst_rcp[1 + Tables::NSUB];
+    __shared__ RankTable lst_rank[1 + Tables::NSUB];
 
     const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5, NT = blockDim.x;
     make_pattern_words(patw, A.k0);
@@ -162,6 +163,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
         lst_m[tid] = l.m;
         lst_gpf[tid] = l.gpf;
         lst_rcp[tid] = l.rcp;
+        lst_rank[tid] = tid == 0 ? A.rk : A.srk[tid - 1];
     }
     u32* my = bits + w * sub_words;
     const u64* my64 = (const u64*)my;
@@ -263,9 +265,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         const u64 b = bb + t;
                         v32 = (u32)(pc_min(pc_max(pi_lookup(A.pit, v), b), A.a) + 1);
                     } else {
-                        const u32 li = (si.flags >> 2) & 7u;
-                        v32 = (u32)rank_lookup(li == 0 ? A.rk : li == 1 ? A.srk[0] : li == 2 ? A.srk[1]
-                                                                  : li == 3 ? A.srk[2] : A.srk[3], v);
+                        v32 = (u32)rank_lookup(lst_rank[(si.flags >> 2) & 7u], v);
                     }
                 }
                 I[idx] = v32;
