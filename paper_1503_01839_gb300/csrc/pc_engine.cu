@@ -184,7 +184,7 @@ u32 default_alpha(u64 x)
     if (d <= 11) return 6;
     if (d <= 13) return 24;
     if (d <= 15) return 28;
-    if (d <= 17) return 24;
+    if (d <= 17) return 32;
     return 48;
 }
 
