@@ -29,6 +29,7 @@ struct LeafArgs {
     const u32* samp;
     u32 samp_s;
     u32 sampled;
+    u32 clust_chunk;   // leaves per clustered chunk (a multiple of 32)
 };
 
 // pi(v) and p_pi(v) from the sampled table: start at pi(floor(v/s) * s), then
@@ -63,6 +64,9 @@ static LeafArgs make_args(pc_ctx* ctx, const LeafProblem& P, u64 n_lim)
     A.samp = ctx->T.samp.as<u32>();
     A.samp_s = ctx->T.samp_s;
     A.sampled = ctx->params.pi_gather == 1;
+    // a lane walks clust_chunk / 32 primes of a clustered chunk: long slices keep
+    // more of a run in one lane, short ones balance the warps when there are few
+    A.clust_chunk = P.x >= 100000000000000000ull ? 16384 : 8192;
     return A;
 }
 
@@ -173,9 +177,8 @@ int run_trivial(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 // grows, and stays >= p_l), so the whole run counts (run length) * (l - b + 2)
 // from two pi lookups and two quotients (p_l is read off the pi record of u).  Those leaves (q^2 >= CLUST_K * x/p_b,
 // i.e. u <= q / CLUST_K) are walked run by run, each thread over a contiguous
-// slice; the rest one leaf per thread.
-static constexpr u32 EASY_CHUNK = 16384;
-static constexpr u32 CLUST_CHUNK = 65536;   // leaves per clustered chunk (256 per thread)
+// slice; the rest one leaf per thread.  Chunks go to warps one at a time.
+static constexpr u32 EASY_CHUNK = 4096;     // leaves per chunk of the rest (128 per lane)
 static constexpr u64 CLUST_K = 2;
 
 struct EasyRange {
@@ -185,9 +188,9 @@ struct EasyRange {
     u32 pad;
 };
 
-__host__ __device__ inline u64 easy_chunks(const EasyRange& r)
+__host__ __device__ inline u64 easy_chunks(const EasyRange& r, u32 clust_chunk)
 {
-    return (r.im - r.i0 + EASY_CHUNK - 1) / EASY_CHUNK + (r.i1 - r.im + CLUST_CHUNK - 1) / CLUST_CHUNK;
+    return (r.im - r.i0 + EASY_CHUNK - 1) / EASY_CHUNK + (r.i1 - r.im + clust_chunk - 1) / clust_chunk;
 }
 
 __global__ void easy_ranges_kernel(LeafArgs A, u64 b_lo, u64 nb, EasyRange* rng, u32* nchunk)
@@ -222,7 +225,7 @@ __global__ void easy_ranges_kernel(LeafArgs A, u64 b_lo, u64 nb, EasyRange* rng,
     }
     if (r.src == 0) r.im = r.i1;
     rng[t] = r;
-    nchunk[t] = (u32)easy_chunks(r);
+    nchunk[t] = (u32)easy_chunks(r, A.clust_chunk);
 }
 
 // chunk -> index t = b - b_lo of the prime whose leaves it holds
@@ -240,14 +243,13 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
                             u64 nchunks, unsigned long long* queue, I128Pair* part)
 {
     __shared__ i128 scratch[32];
-    __shared__ u64 s_ch;
+    const u32 lane = threadIdx.x & 31;
     i64 s = 0;
-    // chunks are handed out one at a time (their costs differ widely)
+    // chunks are handed out one at a time to warps (their costs differ widely)
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_ch = atomicAdd(queue, 1ull);
-        __syncthreads();
-        const u64 ch = s_ch;
+        u64 ch = 0;
+        if (lane == 0) ch = atomicAdd(queue, 1ull);
+        ch = __shfl_sync(0xffffffffu, ch, 0);
         if (ch >= nchunks) break;
         const u64 t = cmap[ch];
         u64 b = b_lo + t;
@@ -258,8 +260,8 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
         u64 xp = div_rcp(A.x, p, A.primes_rcp[b]);
         if (c >= nsp) {
             // clustered chunk: each thread walks the runs of its slice of primes q
-            const u64 per = CLUST_CHUNK / blockDim.x;
-            const u64 start = r.im + (c - nsp) * CLUST_CHUNK + threadIdx.x * per;
+            const u64 per = A.clust_chunk / 32;
+            const u64 start = r.im + (c - nsp) * A.clust_chunk + lane * per;
             const u64 end = pc_min(r.i1, start + per);
             if (start < end) {
                 const u64 qlast = A.primes[end - 1];
@@ -312,7 +314,7 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
         }
         const u64 start = r.i0 + c * EASY_CHUNK;
         const u64 end = pc_min(r.im, start + EASY_CHUNK);
-        for (u64 i = start + threadIdx.x; i < end; i += blockDim.x) {
+        for (u64 i = start + lane; i < end; i += 32) {
             u64 m, v;
             bool neg = true;
             if (r.src) {
