@@ -82,7 +82,7 @@ struct HardArgs {
     u32* counts;
     i32* tallies;
     const HardItem* items;
-    u64 nitems;
+    const unsigned long long* nitems;   // number of items, written by the planner
     I128Pair* acc;                 // one slot per CTA
     u32* queue;
     unsigned long long* stat;      // [0] hard leaves, [1] multiples crossed off
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
         if (tid == 0) s_item = atomicAdd(A.queue, 1u);
         __syncthreads();
         const u64 item = s_item;
-        if (item >= A.nitems) break;
+        if (item >= *A.nitems) break;
         const HardItem it = A.items[item];
         const u64 s = it.s;
         const u32 rep = it.rR >> 16, R = it.rR & 0xFFFFu;
@@ -807,38 +807,111 @@ static u32 pc_sub_bytes(pc_ctx* ctx, u32 seg_bytes)
 // CLEAR_COST.  A segment's crossings are estimated by Mertens' theorem,
 // span * 8/30 * sum_{13 <= p <= P} 1/p ~ span * 8/30 * (ln ln P - 1.0056),
 // P = isqrt(x / L), the largest prime the segment sieves with.
-static void plan_items(const std::vector<u32>& segB, const std::vector<unsigned long long>& est, u32 k0, int ctas,
-                       u64 x, u64 z, u64 span, u64 s0, u64 s1, std::vector<HardItem>& items)
+// Work items, planned on the device.  Cost of a segment (arbitrary units): its
+// (segment, prime) steps, its crossings (span * 8/30 * the sum of 1/p over its
+// primes, about ln ln P - ln ln 11 for primes up to P) and its estimated hard
+// leaves.  A segment whose leaves outweigh both its sieve and a fair share of
+// the launch (total / (4 * resident CTAs)) becomes R replicas that share its
+// leaves.  Items are handed out largest first from an atomic counter, ordered
+// by cost in buckets of a quarter octave (the order only balances the load).
+static constexpr int PLAN_BUCKETS = 128;
+
+struct PlanScratch {
+    double total;                 // cost of every segment of the run
+    unsigned long long nitems;    // items planned
+    u32 cnt[PLAN_BUCKETS];        // items per cost bucket
+    u32 cur[PLAN_BUCKETS];        // next free slot of each bucket
+};
+
+struct PlanArgs {
+    const u32* segB;
+    const unsigned long long* est;
+    u32 k0;
+    double x, z;
+    u64 span, s0, s1;
+    double inv_ctas4;           // 1 / (4 * resident CTAs)
+    u64 cap;                    // slots in items
+    PlanScratch* scr;
+    u32* split;                 // per segment: R | bucket << 16 (R = 0: no item)
+    HardItem* items;
+    unsigned long long* stat;   // [4] items, [5] item steps, [6] set when cap was too small
+};
+
+__device__ __forceinline__ double seg_cost(const PlanArgs& P, u64 s)
 {
-    const double STEP_COST = 128.0, CLEAR_COST = 0.08;
-    const size_t nseg = segB.size();
-    std::vector<double> base(nseg);
-    double total = 0;
-    for (size_t s = s0; s < s1; s++) {
-        const double steps = segB[s] > k0 ? (double)(segB[s] - k0) : 0.0;
-        const u64 P = s ? pc_min(pc_isqrt(x / (s * span)), pc_isqrt(z)) : pc_isqrt(z);
-        const double ll = P > 16 ? std::log(std::log((double)P)) - 1.0056 : 0.0;
-        base[s] = STEP_COST * steps + CLEAR_COST * (double)span * (8.0 / 30.0) * (ll > 0 ? ll : 0.0);
-        total += base[s] + (double)est[s];
+    const double steps = (double)(P.segB[s] - P.k0);
+    const double sz = sqrt(P.z);
+    const double pm = s ? fmin(sqrt(P.x / ((double)s * (double)P.span)), sz) : sz;
+    const double ll = pm > 16.0 ? log(log(pm)) - 1.0056 : 0.0;
+    return 128.0 * steps + 0.08 * (double)P.span * (8.0 / 30.0) * (ll > 0.0 ? ll : 0.0);
+}
+
+__global__ void plan_cost_kernel(PlanArgs P)
+{
+    __shared__ double part[32];
+    double t = 0;
+    for (u64 s = P.s0 + (u64)blockIdx.x * blockDim.x + threadIdx.x; s < P.s1; s += (u64)gridDim.x * blockDim.x)
+        if (P.segB[s] > P.k0) t += seg_cost(P, s) + (double)P.est[s];
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0;
+        for (u32 k = 0; k < blockDim.x / 32; k++) b += part[k];
+        atomicAdd(&P.scr->total, b);
     }
-    const double target = std::max(total / (ctas * 4.0), 1.0);
-    std::vector<std::pair<double, HardItem>> v;
-    v.reserve(s1 - s0 + 64);
-    for (size_t s = s0; s < s1; s++) {
-        if (segB[s] <= k0) continue;
-        u32 R = 1;
-        if (base[s] + (double)est[s] > target && (double)est[s] > base[s]) {
-            // split the leaves while a replica's leaf share still outweighs its sieve
-            const double room = std::max(target - base[s], base[s]);
-            R = (u32)std::min(1024.0, std::ceil((double)est[s] / std::max(room, 1.0)));
-            if (R < 1) R = 1;
+}
+
+// R and the cost bucket of every segment, decided once and stored
+__global__ void plan_split_kernel(PlanArgs P)
+{
+    const double target = fmax(P.scr->total * P.inv_ctas4, 1.0);
+    for (u64 s = P.s0 + (u64)blockIdx.x * blockDim.x + threadIdx.x; s < P.s1; s += (u64)gridDim.x * blockDim.x) {
+        u32 v = 0;
+        if (P.segB[s] > P.k0) {
+            const double base = seg_cost(P, s), e = (double)P.est[s];
+            u32 R = 1;
+            if (base + e > target && e > base) {
+                const double room = fmax(target - base, base);
+                R = (u32)fmin(1024.0, ceil(e / fmax(room, 1.0)));
+                if (R < 1) R = 1;
+            }
+            const int k = (int)floor(4.0 * log2(base + e / R));
+            const u32 key = (u32)(k < 0 ? 0 : (k >= PLAN_BUCKETS ? PLAN_BUCKETS - 1 : k));
+            v = R | (key << 16);
+            atomicAdd(&P.scr->cnt[key], R);
+            atomicAdd(&P.stat[5], (unsigned long long)R * (P.segB[s] - P.k0));
         }
-        for (u32 r = 0; r < R; r++)
-            v.push_back({base[s] + (double)est[s] / R, HardItem{(u32)s, (r << 16) | R}});
+        P.split[s] = v;
     }
-    std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-    items.resize(v.size());
-    for (size_t i = 0; i < v.size(); i++) items[i] = v[i].second;
+}
+
+// first slot of every bucket, the most costly bucket first (one block)
+__global__ void plan_offsets_kernel(PlanArgs P)
+{
+    if (threadIdx.x != 0) return;
+    unsigned long long run = 0;
+    for (int k = PLAN_BUCKETS - 1; k >= 0; k--) {
+        P.scr->cur[k] = (u32)run;
+        run += P.scr->cnt[k];
+    }
+    if (run > P.cap) {   // cannot happen with cap = segments + 8 * CTAs; the run reports it
+        P.stat[6] = 1;
+        run = 0;
+    }
+    P.scr->nitems = run;
+    P.stat[4] = run;
+}
+
+__global__ void plan_scatter_kernel(PlanArgs P)
+{
+    if (P.stat[6]) return;
+    for (u64 s = P.s0 + (u64)blockIdx.x * blockDim.x + threadIdx.x; s < P.s1; s += (u64)gridDim.x * blockDim.x) {
+        const u32 v = P.split[s], R = v & 0xFFFFu;
+        if (!R) continue;
+        const u32 pos = atomicAdd(&P.scr->cur[v >> 16], R);
+        for (u32 r = 0; r < R; r++) P.items[pos + r] = HardItem{(u32)s, (r << 16) | R};
+    }
 }
 
 int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
@@ -892,12 +965,13 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 
     const u64 nrows = bmax - A.k0 + 1;
     PC_TRY(buf_reserve(ctx, ctx->seg_b, A.nseg * sizeof(u32) + (nrows + 1) * sizeof(u32)));
-    PC_TRY(buf_reserve(ctx, ctx->seg_off, (nrows + 1) * sizeof(u64) + 3 * A.nseg * sizeof(u64)));
+    PC_TRY(buf_reserve(ctx, ctx->seg_off, (nrows + 1) * sizeof(u64) + 3 * A.nseg * sizeof(u64) + A.nseg * sizeof(u32)));
     u32* segB = ctx->seg_b.as<u32>();
     u32* rowlen = segB + A.nseg;
     u64* off = ctx->seg_off.as<u64>();
     unsigned long long* est = (unsigned long long*)(off + nrows + 1);
     u64* rcp_seg = (u64*)(est + A.nseg);
+    u32* split = (u32*)(rcp_seg + 2 * A.nseg);   // the work-item split of every segment
     A.rcp_seg = rcp_seg;
     A.rcp_y = ~0ull / P.y;
     seg_b_kernel<<<(unsigned)((A.nseg + 255) / 256), 256, 0, ctx->stream>>>(P.x, A.nseg, A.span, A.bmax, A.pit, segB,
@@ -923,17 +997,6 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
         pc_set_error(ctx, "hard-leaf sieve: %llu count rows exceed 32-bit offsets", (unsigned long long)total);
         return PC_EOVERFLOW;
     }
-
-    // per-segment leaf estimate, then the work items
-    PC_CUDA(ctx, cudaMemsetAsync(est, 0, A.nseg * sizeof(u64), ctx->stream));
-    hard_estimate_kernel<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, total, (u32)nrows, est);
-    PC_LAUNCHED(ctx);
-    ctx->stats.kernel_launches++;
-    std::vector<u32> hsegB(A.nseg);
-    std::vector<unsigned long long> hest(A.nseg);
-    PC_CUDA(ctx, cudaMemcpyAsync(hsegB.data(), segB, A.nseg * sizeof(u32), cudaMemcpyDeviceToHost, ctx->stream));
-    PC_CUDA(ctx, cudaMemcpyAsync(hest.data(), est, A.nseg * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
-    PC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
 
     const u32 nbw = A.sub_bytes >> 7;
     (void)nbw;
@@ -992,27 +1055,41 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     if (per_sm > 4) per_sm = 4;
     int ctas = ctx->sm_count * per_sm;
 
-    std::vector<HardItem> items;
-    plan_items(hsegB, hest, A.k0, ctas, P.x, P.z, A.span, A.s0, A.s1, items);
-    A.nitems = items.size();
-    ctx->stats.work_items = items.size();
-    for (const HardItem& it : items) ctx->stats.item_steps += hsegB[it.s] > A.k0 ? hsegB[it.s] - A.k0 : 0;
+    // per-segment leaf estimate, then the work items, all on the device
+    PC_CUDA(ctx, cudaMemsetAsync(est, 0, A.nseg * sizeof(u64), ctx->stream));
+    hard_estimate_kernel<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, total, (u32)nrows, est);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    const u64 cap = (A.s1 - A.s0) + 8ull * (u64)ctas + 64;
+    const size_t items_bytes = (size_t)ctas * sizeof(I128Pair) + cap * sizeof(HardItem);
     PC_TRY(buf_reserve(ctx, ctx->counts, total * sizeof(u32)));
     PC_TRY(buf_reserve(ctx, ctx->tallies, total * sizeof(i32)));
-    PC_TRY(buf_reserve(ctx, ctx->acc_seg, (size_t)ctas * sizeof(I128Pair) + items.size() * sizeof(HardItem) + 64));
-    PC_TRY(buf_reserve(ctx, ctx->queue, 64));
+    PC_TRY(buf_reserve(ctx, ctx->acc_seg, (items_bytes + 15) / 16 * 16 + sizeof(PlanScratch)));
+    PC_TRY(buf_reserve(ctx, ctx->queue, 128));
     HardItem* ditems = (HardItem*)(ctx->acc_seg.as<I128Pair>() + ctas);
-    if (!items.empty())
-        PC_CUDA(ctx, cudaMemcpyAsync(ditems, items.data(), items.size() * sizeof(HardItem), cudaMemcpyHostToDevice,
-                                     ctx->stream));
-    PC_CUDA(ctx, cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream));
-    PC_CUDA(ctx, cudaMemsetAsync(ctx->tallies.p, 0, total * sizeof(i32), ctx->stream));
+    PlanScratch* scr = (PlanScratch*)(ctx->acc_seg.as<unsigned char>() + (items_bytes + 15) / 16 * 16);
     A.counts = ctx->counts.as<u32>();
     A.tallies = ctx->tallies.as<i32>();
     A.items = ditems;
+    A.nitems = &scr->nitems;
     A.acc = ctx->acc_seg.as<I128Pair>();
     A.queue = ctx->queue.as<u32>();
     A.stat = (unsigned long long*)(ctx->queue.as<u32>() + 2);
+    PC_CUDA(ctx, cudaMemsetAsync(ctx->queue.p, 0, 128, ctx->stream));
+    PC_CUDA(ctx, cudaMemsetAsync(scr, 0, sizeof(PlanScratch), ctx->stream));
+    PC_CUDA(ctx, cudaMemsetAsync(ctx->tallies.p, 0, total * sizeof(i32), ctx->stream));
+    PlanArgs PA{segB, est, A.k0, (double)P.x, (double)P.z, A.span, A.s0, A.s1, 1.0 / (4.0 * ctas), cap,
+                scr, split, ditems, A.stat};
+    const unsigned pg = (unsigned)pc_min((A.s1 - A.s0 + 255) / 256, (u64)ctx->sm_count * 4);
+    plan_cost_kernel<<<pg, 256, 0, ctx->stream>>>(PA);
+    PC_LAUNCHED(ctx);
+    plan_split_kernel<<<pg, 256, 0, ctx->stream>>>(PA);
+    PC_LAUNCHED(ctx);
+    plan_offsets_kernel<<<1, 32, 0, ctx->stream>>>(PA);
+    PC_LAUNCHED(ctx);
+    plan_scatter_kernel<<<pg, 256, 0, ctx->stream>>>(PA);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches += 4;
 
     cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
     PC_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
@@ -1029,8 +1106,14 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     PC_TRY(reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out));
     PC_TRY(reduce_i128(ctx, A.acc, ctas, out));
 
-    u64 nl[4] = {0, 0, 0, 0};
-    PC_TRY(copy_to_host(ctx, nl, A.stat, 4 * sizeof(u64)));
+    u64 nl[7] = {0, 0, 0, 0, 0, 0, 0};
+    PC_TRY(copy_to_host(ctx, nl, A.stat, 7 * sizeof(u64)));
+    if (nl[6]) {
+        pc_set_error(ctx, "hard-leaf sieve: work items exceed the planned %llu slots", (unsigned long long)cap);
+        return PC_EOVERFLOW;
+    }
+    ctx->stats.work_items = nl[4];
+    ctx->stats.item_steps += nl[5];
     ctx->stats.warp_steps += nl[2];
     ctx->stats.leaf_warp_steps += nl[3];
     float ms = 0;
