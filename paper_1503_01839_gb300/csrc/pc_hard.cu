@@ -1052,7 +1052,7 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
         return PC_EINVAL;
     }
     if (want && per_sm > want) per_sm = want;
-    if (per_sm > 4) per_sm = 4;
+    if (per_sm > 8) per_sm = 8;   // 32 KiB segments fit 4; smaller ones (autotuned, or set) up to 8
     int ctas = ctx->sm_count * per_sm;
 
     // per-segment leaf estimate, then the work items, all on the device
