@@ -74,19 +74,15 @@ PC_HD u64 pc_min(u64 a, u64 b) { return a < b ? a : b; }
 
 // Division by an invariant divisor through a precomputed reciprocal
 // (Granlund and Montgomery, "Division by invariant integers using
-// multiplication", PLDI 1994): v = floor((2^64 - 1) / d) for d >= 1.  Then
-// q = floor(n * v / 2^64) is floor(n / d) or one less (v <= 2^64 / d, and
-// n * v / 2^64 > n / d - 1 for n < 2^64); the remainder test fixes it.
+// multiplication", PLDI 1994): v = floor((2^64 - 1) / d) for d >= 1.  For
+// n < 2^63, n / d - 1 < n * v / 2^64 <= n / d (v > (2^64 - 1 - d) / d and
+// (1 + d) / d <= 2 give n * v / 2^64 > n / d - n / 2^63), so
+// q = floor(n * v / 2^64) is floor(n / d) or one less, and one remainder test
+// fixes it.  Every dividend in this library is at most x < 2^63.
 __device__ __forceinline__ u64 div_rcp(u64 n, u64 d, u64 v)
 {
-    u64 q = __umul64hi(n, v);
-    u64 r = n - q * d;
-    if (r >= d) {
-        q++;
-        r -= d;
-    }
-    if (r >= d) q++;
-    return q;
+    const u64 q = __umul64hi(n, v);
+    return n - q * d >= d ? q + 1 : q;
 }
 PC_HD u64 pc_max(u64 a, u64 b) { return a > b ? a : b; }
 
