@@ -104,11 +104,12 @@ struct PiTable {
 // pi(v) for 0 <= v <= limit.
 __device__ __forceinline__ u64 pi_lookup(const PiTable& t, u64 v)
 {
-    const u64 small = (v >= 2) + (v >= 3) + (v >= 5);
-    const u64 w = v / 240;
-    const u32 r = (u32)(v - w * 240);
-    const u32 e = 8 * (r / 30) + cntle30(r % 30);
-    const uint4 q = __ldg((const uint4*)(t.rec + w));
+    // v <= limit < 2^32; one division by 30 gives the record (8 groups of 30
+    // integers each) and the bit inside it
+    const u32 v32 = (u32)v, q30 = v32 / 30;
+    const u64 small = (v32 >= 2) + (v32 >= 3) + (v32 >= 5);
+    const u32 e = 8 * (q30 & 7) + cntle30(v32 - 30 * q30);
+    const uint4 q = __ldg((const uint4*)(t.rec + (q30 >> 3)));
     const u64 bits = (u64)q.x | ((u64)q.y << 32);
     const u64 mask = e >= 64 ? ~0ull : ((1ull << e) - 1);
     return small + q.z + __popcll(bits & mask);

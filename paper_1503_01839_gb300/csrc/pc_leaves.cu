@@ -273,9 +273,10 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
                         l = pi_sampled(A, u, &pl);
                     } else {
                         // pi(u) from u's record (u >= p_b >= 13, so 2, 3 and 5 all count)
-                        w = u / 240;
-                        const u32 rr = (u32)(u - w * 240);
-                        const u32 e = 8 * (rr / 30) + cntle30(rr % 30);
+                        // u < y < 2^32: the record is u / 240, its bit from u / 30 and u % 30
+                        const u32 u32v = (u32)u, q30 = u32v / 30;
+                        w = q30 >> 3;
+                        const u32 e = 8 * (q30 & 7) + cntle30(u32v - 30 * q30);
                         const uint4 rq = __ldg((const uint4*)(A.pit.rec + w));
                         bits = ((u64)rq.x | ((u64)rq.y << 32)) & (e >= 64 ? ~0ull : ((1ull << e) - 1ull));
                         l = 3 + rq.z + __popcll(bits);
@@ -335,8 +336,8 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
                 u64 pv;
                 piu = pi_sampled(A, u, &pv);
             } else {
-                const u32 w = u / 240, rr = u - w * 240;
-                const u32 e = 8 * (rr / 30) + cntle30(rr % 30);   // 0..64
+                const u32 q30 = u / 30, w = q30 >> 3;
+                const u32 e = 8 * (q30 & 7) + cntle30(u - 30 * q30);   // 0..64
                 const uint4 q = __ldg((const uint4*)(A.pit.rec + w));
                 u32 c;
                 if (e <= 32) c = __popc(q.x & (e == 32 ? ~0u : (1u << e) - 1u));
