@@ -101,6 +101,15 @@ struct PiTable {
     u64 limit;
 };
 
+// The low e bits (0 <= e <= 64) of w, moved to the top of the word: a left
+// shift by 64 - e, which PTX clamps at 64 (the result is then 0).
+__device__ __forceinline__ u64 low_bits_top(u64 w, u32 e)
+{
+    u64 r;
+    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(w), "r"(64u - e));
+    return r;
+}
+
 // pi(v) for 0 <= v <= limit.
 __device__ __forceinline__ u64 pi_lookup(const PiTable& t, u64 v)
 {
@@ -110,9 +119,7 @@ __device__ __forceinline__ u64 pi_lookup(const PiTable& t, u64 v)
     const u64 small = (v32 >= 2) + (v32 >= 3) + (v32 >= 5);
     const u32 e = 8 * (q30 & 7) + cntle30(v32 - 30 * q30);
     const uint4 q = __ldg((const uint4*)(t.rec + (q30 >> 3)));
-    const u64 bits = (u64)q.x | ((u64)q.y << 32);
-    const u64 mask = e >= 64 ? ~0ull : ((1ull << e) - 1);
-    return small + q.z + __popcll(bits & mask);
+    return small + q.z + __popcll(low_bits_top((u64)q.x | ((u64)q.y << 32), e));
 }
 
 // rank structure over a plain bitset of [0, limit]: rank(v) = #set bits <= v.

@@ -269,6 +269,7 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
                 for (u64 i = start; i < end;) {
                     const u64 u = div_rcp(xp, A.primes[i], A.primes_rcp[i]);
                     u64 l, pl = 0, w = 0, bits = 0;
+                    u32 hb0 = 0;
                     if (SAMPLED) {
                         l = pi_sampled(A, u, &pl);
                     } else {
@@ -278,15 +279,17 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
                         w = q30 >> 3;
                         const u32 e = 8 * (q30 & 7) + cntle30(u32v - 30 * q30);
                         const uint4 rq = __ldg((const uint4*)(A.pit.rec + w));
-                        bits = ((u64)rq.x | ((u64)rq.y << 32)) & (e >= 64 ? ~0ull : ((1ull << e) - 1ull));
+                        // the bits of the primes <= u, at the top of the word (shifted by 64 - e)
+                        bits = low_bits_top((u64)rq.x | ((u64)rq.y << 32), e);
                         l = 3 + rq.z + __popcll(bits);
+                        hb0 = e - 1;
                     }
                     u64 n = 1;
                     if (i + 1 < end) {
                         if (!SAMPLED) {
                             // p_l, the largest prime <= u, from the same record when it holds one
                             if (bits) {
-                                const u32 hb = 63 - __clzll((long long)bits);
+                                const u32 hb = hb0 - __clzll((long long)bits);   // its bit in the record
                                 pl = 240 * w + 30 * (hb >> 3) + r8(hb & 7);
                             } else {
                                 pl = A.primes[l];
@@ -339,9 +342,7 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
                 const u32 q30 = u / 30, w = q30 >> 3;
                 const u32 e = 8 * (q30 & 7) + cntle30(u - 30 * q30);   // 0..64
                 const uint4 q = __ldg((const uint4*)(A.pit.rec + w));
-                u32 c;
-                if (e <= 32) c = __popc(q.x & (e == 32 ? ~0u : (1u << e) - 1u));
-                else c = __popc(q.x) + __popc(q.y & (e == 64 ? ~0u : (1u << (e - 32)) - 1u));
+                const u32 c = __popcll(low_bits_top((u64)q.x | ((u64)q.y << 32), e));
                 const u32 small = b > 3 ? 3u : (u >= 2) + (u >= 3) + (u >= 5);
                 piu = small + q.z + c;
             }
