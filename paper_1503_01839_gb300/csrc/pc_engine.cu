@@ -184,7 +184,8 @@ u32 default_alpha(u64 x)
     if (d <= 11) return 6;
     if (d <= 13) return 24;
     if (d <= 15) return 28;
-    if (d <= 17) return 32;
+    if (d == 16) return 32;
+    if (d == 17) return 40;
     return 48;
 }
 
