@@ -479,7 +479,10 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         }
                         const u64 xp = st[t].xp;
                         auto one_leaf = [&](u32 info, u32 m32, u64 v, u32 gpf) {
-                            if (!m32 || (info >> 1) <= b || (A.trunc && gpf > A.a)) return;
+                            // no early exit: a lane without a leaf of b (no entry, lpf <= p_b, or
+                            // gpf > p_a) runs the same code and adds 0; its block index is clamped
+                            // below and its shifts to 0..64, so its reads stay inside the sub-range
+                            const bool valid = m32 && (info >> 1) > b && !(A.trunc && gpf > A.a);
                             const bool neg = info & 1u;
                             const u64 u = div_rcp(xp, m32, v);
                             const u32 e = seg_count_end(u, Lw);
@@ -500,9 +503,10 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                                 return __popcll(r);
                             };
                             const u32 c = mypre[bi] + part(h0.x, 0) + part(h0.y, 1) + part(h1.x, 2) + part(h1.y, 3);
-                            acc += neg ? (i64)c : -(i64)c;
-                            tl += neg ? 1 : -1;
-                            nleaves++;
+                            const i64 sg = valid ? (neg ? 1 : -1) : 0;
+                            acc += sg * (i64)c;
+                            tl += (int)sg;
+                            nleaves += valid;
                         };
                         one_leaf(pf_info, pf_m, pf_v, pf_gpf);                        // first 32, loaded ahead
                         const u64 later = leafy & ~((2ull << t) - 1);
