@@ -391,10 +391,9 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         i32 by = basew[tt * nw + w] + (i32)st[tt].coff[j] + (r8(j) < kmod ? p : 0);
                         for (; by < (i32)sub_bytes; by += p) {
                             const u32 pos = ((u32)by << 3) + bj, mask = 1u << (pos & 31);
-                            if (atomicAnd(&my[pos >> 5], ~mask) & mask) {
-                                d++;
-                                atomicSub(&myblk32[pos >> 9], 1u << (16 * ((pos >> 8) & 1)));
-                            }
+                            const u32 hit = (atomicAnd(&my[pos >> 5], ~mask) & mask) ? 1u : 0u;
+                            d += hit;
+                            atomicSub(&myblk32[pos >> 9], hit << (16 * ((pos >> 8) & 1)));   // 0 or 1
                             nclears++;
                         }
                         const u32 ps = st[tt].pself;
@@ -540,11 +539,10 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                     auto clear_bit = [&](u32 pos) {   // pos: bit inside this warp's sub-range
                         const u32 mask = 1u << (pos & 31);
                         const u32 old = my[pos >> 5];
-                        if (old & mask) {
-                            my[pos >> 5] = old & ~mask;
-                            dec++;
-                            if (!recount) atomicSub(&myblk32[pos >> 9], 1u << (16 * ((pos >> 8) & 1)));
-                        }
+                        my[pos >> 5] = old & ~mask;   // written back whether or not the bit was set
+                        const u32 hit = (old & mask) ? 1u : 0u;
+                        dec += hit;
+                        if (!recount) atomicSub(&myblk32[pos >> 9], hit << (16 * ((pos >> 8) & 1)));
                     };
                     {
                         if (base < (i32)sub_bytes) {
@@ -564,17 +562,15 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                                 for (; by + step4 < (i32)sub_bytes; by += 2 * step4, n += 2) {
                                     const u32 pa = ((u32)by << 3) + bj, pb = ((u32)(by + step4) << 3) + bj;
                                     const u32 ma = 1u << (pa & 31), mb = 1u << (pb & 31);
+                                    // no branch on whether the bit was still set: the word is
+                                    // written back either way and the block counter takes 0 or 1
                                     const u32 oa = my[pa >> 5], ob = my[pb >> 5];
-                                    if (oa & ma) {
-                                        my[pa >> 5] = oa & ~ma;
-                                        dec++;
-                                        atomicSub(&myblk32[pa >> 9], 1u << (16 * ((pa >> 8) & 1)));
-                                    }
-                                    if (ob & mb) {
-                                        my[pb >> 5] = ob & ~mb;
-                                        dec++;
-                                        atomicSub(&myblk32[pb >> 9], 1u << (16 * ((pb >> 8) & 1)));
-                                    }
+                                    my[pa >> 5] = oa & ~ma;
+                                    my[pb >> 5] = ob & ~mb;
+                                    const u32 ca = (oa & ma) ? 1u : 0u, cb = (ob & mb) ? 1u : 0u;
+                                    dec += ca + cb;
+                                    atomicSub(&myblk32[pa >> 9], ca << (16 * ((pa >> 8) & 1)));
+                                    atomicSub(&myblk32[pb >> 9], cb << (16 * ((pb >> 8) & 1)));
                                 }
                                 if (by < (i32)sub_bytes) {
                                     clear_bit(((u32)by << 3) + bj);
