@@ -179,7 +179,7 @@ int run_trivial(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 // i.e. u <= q / CLUST_K) are walked run by run, each thread over a contiguous
 // slice; the rest one leaf per thread.  Chunks go to warps one at a time.
 static constexpr u32 EASY_CHUNK = 4096;     // leaves per chunk of the rest (128 per lane)
-static constexpr u64 CLUST_K = 2;
+static constexpr u64 CLUST_K = 3;
 
 struct EasyRange {
     u64 i0, i1;   // list indices [i0, i1) or prime indices (i0, i1] shifted to [i0+1, i1+1)
