@@ -8,7 +8,7 @@
  * refines (Sections 2-4): ordinary leaves, special leaves split into
  * trivial / easy / hard leaves, and the second partial sum P2.  The hard
  * special leaves are resolved by a segmented sieve held in GPU shared memory
- * (the "main sieve" of Section 3), whose per-segment counts are stitched
+ * (the main sieve of Section 3), whose per-segment counts are stitched
  * together by a device-wide carry scan (the tallies of Section 3).
  *
  * Conventions shared by every call:

@@ -21,8 +21,8 @@
 // Across segments, phi(L_s - 1, b - 1) = sum_{s' < s} count(s', b - 1) is an
 // exclusive scan (the carries), and
 //   S2_hard = sum (local sums) + sum_{s,b} tally(s, b) * phi(L_s - 1, b - 1).
-// All segments are sieved at once, so the "synchronization after each
-// round" of Section 3 becomes one scan.
+// All segments are sieved at once, so the per-round synchronization of the
+// blocks in Section 3 becomes one scan.
 //
 // A hard leaf (b, m) has u < x / p_b^2, so a segment starting at L only
 // needs the primes p_b <= isqrt(x / L): B_s = pi(isqrt(x/L)).
@@ -32,7 +32,8 @@
 // the leaves of every segment; heavy segments are handed to several CTAs
 // ("replicas"), each of which sieves the whole segment but resolves only its
 // share of every step's leaves (Section 3 mentions dynamic block scheduling;
-// here the schedule is a list of work items sorted by estimated cost).
+// here the schedule is a list of work items ordered by estimated cost,
+// planned on the device).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -117,13 +118,14 @@ __device__ __forceinline__ bool leaf_window(const HardArgs& A, u64 p, u64 vp, u6
     return mhi > mlo;
 }
 
-// Crossing off needs no atomics: a warp owns its sub-range.  For a prime
-// below seg_bytes/4 the lanes take whole wheel rounds (30 p integers, p
-// bytes), even rounds first, then odd ones, so lanes of one pass touch words
-// at least 2p bytes apart.  Larger primes have at most 48 multiples in the
-// segment; the CTA lists them once per batch ("events") and each warp applies
-// those in its sub-range.  Multiples of one prime are >= p integers apart, so
-// lanes never share a word there either.
+// A warp owns its sub-range, so crossing off one prime needs no atomics on
+// the bitset.  For p < 128 the lanes take whole wheel rounds (30 p integers,
+// p bytes), even rounds first, then odd ones, so lanes of one pass touch
+// words at least 2p bytes apart; for larger p a lane takes one residue class
+// in every fourth round, and two of its crossings by different lanes are at
+// least 4 bytes apart.  Runs of steps crossed off together (group_cross) mix
+// primes in one pass and use atomics on the words.  Block counters take
+// shared-memory atomics, since lanes of one pass may share a block.
 // Instantiated for several (threads, resident CTAs) launch bounds: fewer
 // registers per thread buy more resident warps to hide shared-memory latency.
 template <int MAXT, int MINB>
@@ -297,7 +299,8 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
             __syncthreads();
             // C: every warp runs the batch over its own sub-range.  Steps that touch
             // neither its leaves nor its integers are skipped: the warp marks its
-            // busy steps with two ballots and fills the skipped counts afterwards.
+            // busy steps (and those with leaves, and those it may cross off in a
+            // group) with ballots and fills the skipped counts afterwards.
             auto leaf_range = [&](u32 t, u32& j0, u32& j1) {
                 j0 = I[t * (nw + 1) + w + 1];
                 j1 = I[t * (nw + 1) + w];
