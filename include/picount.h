@@ -258,10 +258,10 @@ void pc_server_destroy(pc_server* s);
  * Computes P2(x, a), a = pi(y), as pc_p2 does:
  *   x, y       iroot3(x) <= y <= isqrt(x), x < 2^63 (PC_ERANGE otherwise);
  *   primes     device array of the primes 2, 3, 5, ... in ascending order,
- *              n_primes entries: every prime <= isqrt(x) and at least one
- *              prime above it (so the array provably covers isqrt(x));
+ *              n_primes entries, every prime <= isqrt(x); the last entry
+ *              must be >= isqrt(x) (then the array provably covers isqrt(x));
  *   out        device uint64_t that receives P2; it receives UINT64_MAX if
- *              the last entry of primes is not above isqrt(x);
+ *              the last entry of primes is below isqrt(x);
  *   stream     cudaStream_t (NULL = legacy default stream) of the current
  *              device.
  * The work is enqueued on `stream` and the call returns without waiting; *out

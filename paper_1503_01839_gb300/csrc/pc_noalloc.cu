@@ -107,10 +107,10 @@ __global__ void __launch_bounds__(NA_THREADS) na_p2_sieve_kernel(NaArgs A)
             }
         }
         __syncthreads();
-        for (u32 k = tid; k < nblk; k += NA_THREADS) {
-            u32 c = 0;
-            for (u32 w = 0; w < 32; w++) c += __popc(bits[32 * k + w]);
-            blk[k] = c;
+        // one warp per 1024-bit block: lane l reads word 32k + l (32 banks, no conflict)
+        for (u32 k = wid; k < nblk; k += NA_THREADS / 32) {
+            const u32 c = __reduce_add_sync(0xffffffffu, (u32)__popc(bits[32 * k + lane]));
+            if (lane == 0) blk[k] = c;
         }
         __syncthreads();
         if (wid == 0) {   // nblk = 256: eight blocks per lane
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(1024) na_p2_combine_kernel(NaArgs A, u64* out)
         const u64 B = count_le(A.P, A.n, pc_isqrt(A.z));
         const u64 a = count_le(A.P, A.n, A.y);
         const u64 K = count_le(A.P, A.n, A.r);
-        const bool ok = A.n > 0 && (u64)A.P[A.n - 1] > A.r;   // the caller's primes run past isqrt(x)
+        const bool ok = A.n > 0 && (u64)A.P[A.n - 1] >= A.r;   // the caller's primes reach isqrt(x)
         i128 v = dot;
         if (K > a) {
             const i128 nq = (i128)(K - a);

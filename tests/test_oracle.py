@@ -84,6 +84,24 @@ def test_pi_sieve_small_exhaustive():
         assert o.pi_sieve(x) == pi_small(x)
 
 
+def test_nth_prime_vs_sieve_list():
+    # p_k by the plain sieve list: every k up to 2000, then a sample up to 10^4
+    for k in range(1, 2001):
+        assert o.nth_prime(k) == PR[k - 1], k
+    rng = random.Random(11)
+    for k in rng.sample(range(2001, 10001), 300) + [10000]:
+        assert o.nth_prime(k) == PR[k - 1], k
+
+
+def test_nth_prime_table1(pi_pow10):
+    # Table 1 fixes p_k at k = pi(10^n): the largest prime <= 10^n, the next one above it
+    assert o.nth_prime(168) == 997 and pi_pow10[3] == 168
+    assert o.nth_prime(78498) == 999983 and pi_pow10[6] == 78498
+    for n in range(1, 9):
+        k = pi_pow10[n]
+        assert o.nth_prime(k) <= 10 ** n < o.nth_prime(k + 1), n
+
+
 def test_phi_brute_definition_small():
     # direct gcd count against the definition of phi(x, a) (Section 3)
     for x in range(0, 400, 7):
