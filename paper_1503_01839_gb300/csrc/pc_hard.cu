@@ -48,6 +48,10 @@ static_assert(GROUP_P >= RECOUNT_P, "grouped steps keep their block counters up 
 static constexpr u32 MAX_NW = 16;       // warps (sub-ranges) per segment
 static constexpr u32 MAX_SUB = 8192;    // bytes per sub-range: up to 256 blocks of 256 bits
 static constexpr u32 MAX_SEG = 131072;  // bytes per segment
+// Steps of primes p >= sub-range bytes (at most one multiple per residue class in a
+// sub-range) with p^3 above the segment are taken in runs (sparse_runs below):
+static constexpr u32 RUN_LEAVES = 32;   // a run ends after the step that brings its leaves to this many
+static constexpr u32 LOG_CAP = 32 * 9;  // hit log entries per warp: 32 steps x (8 classes + p itself)
 
 struct HardItem {
     u32 s;    // segment
@@ -99,7 +103,8 @@ struct __align__(16) StepInfo {
     u32 coff[8];   // floor(p * R8[j] / 30): byte offset of class j inside a wheel round
     u8 cbit[8];    // bit of class j inside its byte
     u32 flags;     // bit 0: leaves are primes, bit 1: step has leaves, bits 2-4: m-list (0 = all, k = sub-list k-1),
-                   // bit 5: p >= GROUP_P and p^3 > the last integer of the segment (see group_cross)
+                   // bit 5: p >= GROUP_P and p^3 > the last integer of the segment (see group_cross),
+                   // bit 6: bit 5 and p >= the sub-range's bytes (see sparse_runs)
     u32 pself;     // segment bit of p_b itself, or ~0
     u32 row;       // off[b - k0]: start of the count / tally rows of b
     u32 pad[3];
@@ -144,6 +149,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
     i32* tw = (i32*)(cw + BATCH * nw);             // BATCH * nw
     i32* basew = tw + BATCH * nw;                  // BATCH * nw
     u8* kmodw = (u8*)(basew + BATCH * nw);         // BATCH * nw
+    u16* hitlog = (u16*)(kmodw + BATCH * nw);      // nw * LOG_CAP
 
     __shared__ u32 patw[80];
     __shared__ u32 prev[MAX_NW];
@@ -172,6 +178,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
     u16* myblk = blk + w * nbw;
     u32* myblk32 = (u32*)myblk;
     u16* mypre = pre + w * nbw;
+    u16* lg = hitlog + w * LOG_CAP;
     // count the set bits of every 256-bit block of the sub-range into myblk;
     // returns this lane's share of the total.  Lanes read consecutive 16-byte
     // halves of blocks (no bank conflicts) and pairs of lanes add up a block.
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         if (A.slK[k] <= b) li = k + 1;
                     si.flags = 2u | (p * p > A.y ? 1u : 0u) | (li << 2);
                 }
-                if (p >= GROUP_P && p * p > div_rcp(L + A.span - 1, p, vp)) si.flags |= 32u;
+                if (p >= GROUP_P && p * p > div_rcp(L + A.span - 1, p, vp)) si.flags |= p >= A.sub_bytes ? 96u : 32u;
                 for (int j = 0; j < 8; j++) {
                     const u32 pr = (u32)p * r8(j);
                     si.coff[j] = pr / 30;
@@ -311,15 +318,16 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                     j1 = a1;
                 }
             };
-            u64 busy = 0, leafy = 0, grp = 0;
+            u64 busy = 0, leafy = 0, grp = 0, sparse = 0;
             u32 lj0[BATCH / 32], lj1[BATCH / 32];   // leaf range of step h*32 + lane
 #pragma unroll
             for (u32 h = 0; h < BATCH / 32; h++) {
                 const u32 t = h * 32 + lane;
-                bool on = false, g = false;
+                bool on = false, g = false, sq = false;
                 lj0[h] = lj1[h] = 0;
                 if (t < nb) {
                     const u32 b = bb + t, fl = st[t].flags, ps = st[t].pself;
+                    sq = (fl & 64u) != 0;
                     if (b < Bs) {
                         if (basew[t * nw + w] < (i32)sub_bytes) on = true;
                         if (ps != ~0u && (ps >> A.sub_shift) == w) on = true;
@@ -334,8 +342,13 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 busy |= (u64)__ballot_sync(0xffffffffu, on) << (h * 32);
                 leafy |= (u64)__ballot_sync(0xffffffffu, lj1[h] > lj0[h]) << (h * 32);
                 grp |= (u64)__ballot_sync(0xffffffffu, g) << (h * 32);
+                sparse |= (u64)__ballot_sync(0xffffffffu, sq) << (h * 32);
             }
-            grp &= busy & ~leafy;
+            // the sparse steps are a suffix of the batch (both of their conditions grow with p):
+            // steps below t_sp go one by one or in groups, the rest in runs
+            const u32 t_sp = sparse ? (u32)__ffsll((long long)sparse) - 1 : nb;
+            const u64 lomask = t_sp >= 64 ? ~0ull : (1ull << t_sp) - 1;
+            grp &= busy & ~leafy & lomask;
             // Leaf data (m, its reciprocal, lpf index and mu) does not depend on the
             // sieve, so the first 32 leaves of the next leaf step are loaded ahead,
             // while the warp is still crossing off earlier primes.
@@ -366,9 +379,66 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                     }
                 }
             };
+            // prefix counts of the 256-bit blocks of the sub-range (from the block counters)
+            auto block_prefix = [&]() {
+                if (bpl == 8) {   // one 16-byte load and store per lane
+                    const uint4 q = ((const uint4*)myblk)[lane];
+                    const u32 c01 = (q.x & 0xFFFFu) + (q.x >> 16), c23 = (q.y & 0xFFFFu) + (q.y >> 16);
+                    const u32 c45 = (q.z & 0xFFFFu) + (q.z >> 16), c67 = (q.w & 0xFFFFu) + (q.w >> 16);
+                    const u32 own = c01 + c23 + c45 + c67;
+                    u32 incl = own;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const u32 r0 = incl - own, r2 = r0 + c01, r4 = r2 + c23, r6 = r4 + c45;
+                    uint4 o4;
+                    o4.x = r0 | ((r0 + (q.x & 0xFFFFu)) << 16);
+                    o4.y = r2 | ((r2 + (q.y & 0xFFFFu)) << 16);
+                    o4.z = r4 | ((r4 + (q.z & 0xFFFFu)) << 16);
+                    o4.w = r6 | ((r6 + (q.w & 0xFFFFu)) << 16);
+                    ((uint4*)mypre)[lane] = o4;
+                } else {
+                    u32 run = 0;
+                    for (u32 k = 0; k < bpl; k++) run += myblk[lane * bpl + k];
+                    u32 incl = run;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    run = incl - run;
+                    for (u32 k = 0; k < bpl; k++) {
+                        const u32 bi = lane * bpl + k;
+                        mypre[bi] = (u16)run;
+                        run += myblk[bi];
+                    }
+                }
+                __syncwarp();
+            };
+            // set bits of the sub-range up to the count end e (0 < e <= sub_bits; other lanes
+            // read clamped, in-bounds words and add what they like)
+            auto count_to = [&](u32 e) -> u32 {
+                u32 bi = e >> 8;
+                if (bi >= nbw) bi = nbw - 1;
+                // set bits of block bi below the end (0..256 of them): both halves
+                // of the block at once, no data-dependent loop.  Word i keeps its
+                // bits below rem - 64 i by a left shift of 64 (i + 1) - rem, taken
+                // as at least 0; PTX clamps a 64-bit shift above 64 to 64 (result 0).
+                const u32 rem = e - (bi << 8);
+                const ulonglong2 h0 = ((const ulonglong2*)my64)[2 * bi];
+                const ulonglong2 h1 = ((const ulonglong2*)my64)[2 * bi + 1];
+                auto part = [&](u64 wv, u32 i) -> u32 {
+                    i32 sh = (i32)(64 * i + 64) - (i32)rem;
+                    sh = sh < 0 ? 0 : (sh > 64 ? 64 : sh);
+                    u64 r;
+                    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(wv), "r"(sh));
+                    return __popcll(r);
+                };
+                return mypre[bi] + part(h0.x, 0) + part(h0.y, 1) + part(h1.x, 2) + part(h1.y, 3);
+            };
             nbusy += __popcll(busy);
             nleafy += __popcll(leafy);
-            if (leafy) prefetch(__ffsll((long long)leafy) - 1);
+            if (leafy & lomask) prefetch(__ffsll((long long)(leafy & lomask)) - 1);
             __syncwarp();
             // A run of consecutive busy steps without leaves in this sub-range, all of
             // primes p with p >= GROUP_P and p^3 > every integer of the segment, is
@@ -420,8 +490,139 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 }
                 __syncwarp();
             };
+            // Runs of sparse steps (p >= the sub-range's bytes, so each residue class has at
+            // most one multiple in the sub-range, and p^3 above the segment's last integer).
+            // As in group_cross, a bit still set when the run starts is reached by exactly one
+            // crossing of the run, that of its least prime factor, so every crossing of every
+            // step of the run is found against the bitset as it is at the run's start, in
+            // parallel: lane = (step, residue class), four steps per pass.  The crossings that
+            // hit a set bit go to a log, ordered by step.  A leaf of step t needs the count of
+            // set bits up to u after the steps before t; that is the count on the run's starting
+            // bitset less the logged hits of the run's steps before t below u.  So the leaves of
+            // all steps of a run share 32-lane passes, one block prefix serves the whole run, and
+            // the logged bits are cleared once at its end.  A run ends after the step that
+            // brings its leaves to RUN_LEAVES (or at 32 steps), which keeps the log scans short.
+            auto sparse_runs = [&](u32 t0) {
+                while (t0 < nb) {
+                    // the leaf ranges of the next (up to) 32 steps, one per lane
+                    const u32 ts = t0 + lane;
+                    u32 j0 = 0, j1 = 0;
+                    {
+                        const u32 src = ts & 31;
+                        const u32 a0 = __shfl_sync(0xffffffffu, lj0[0], src), a1 = __shfl_sync(0xffffffffu, lj0[1], src);
+                        const u32 c0 = __shfl_sync(0xffffffffu, lj1[0], src), c1 = __shfl_sync(0xffffffffu, lj1[1], src);
+                        if (ts < nb) {
+                            j0 = ts >= 32 ? a1 : a0;
+                            j1 = ts >= 32 ? c1 : c0;
+                        }
+                    }
+                    const u32 n = j1 - j0;   // 0 for steps without leaves in this sub-range (or share)
+                    u32 incl = n;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const u32 avail = nb - t0 < 32 ? nb - t0 : 32;
+                    const u32 enough = __ballot_sync(0xffffffffu, lane < avail && incl >= RUN_LEAVES);
+                    const u32 len = enough ? (u32)__ffs(enough) : avail;   // steps t0 .. t0 + len - 1
+                    const u32 TL = __shfl_sync(0xffffffffu, incl, len - 1);
+                    const u32 loff = incl - n;                             // first leaf of step t0 + lane
+                    // crossings against the starting bitset; hits logged in step order
+                    u32 nent = 0, hoff = 0;                                // hoff: log entries before step t0 + lane
+                    for (u32 c = 0; c < len; c += 4) {
+                        const u32 sl = lane >> 3, j = lane & 7, i = c + sl, t = t0 + i;
+                        u32 h = 0, pa = 0, pb = 0;
+                        if (i < len && bb + t < Bs) {
+                            const i32 p = (i32)st[t].p;
+                            const i32 by = basew[t * nw + w] + (i32)st[t].coff[j] + (r8(j) < kmodw[t * nw + w] ? p : 0);
+                            if (by < (i32)sub_bytes) {
+                                const u32 pos = ((u32)by << 3) + st[t].cbit[j];
+                                nclears++;
+                                if ((my[pos >> 5] >> (pos & 31)) & 1u) {
+                                    pa = pos;
+                                    h = 1;
+                                }
+                            }
+                            const u32 ps = st[t].pself;
+                            if (j == 0 && ps != ~0u && (ps >> A.sub_shift) == w) {   // p itself
+                                const u32 pos = ps & (sub_bits - 1);
+                                if ((my[pos >> 5] >> (pos & 31)) & 1u) {
+                                    if (h) pb = pos; else pa = pos;
+                                    h++;
+                                }
+                            }
+                        }
+                        const u32 m1 = __ballot_sync(0xffffffffu, h >= 1), m2 = __ballot_sync(0xffffffffu, h >= 2);
+                        const u32 below = (1u << lane) - 1u;
+                        const u32 off = nent + __popc(m1 & below) + __popc(m2 & below);
+                        if (h >= 1) lg[off] = (u16)pa;
+                        if (h >= 2) lg[off + 1] = (u16)pb;
+                        // step c + s starts at the entry offset of lane 8 s
+                        const u32 first = __shfl_sync(0xffffffffu, off, ((lane - c) & 3) * 8);
+                        if (lane >= c && lane < c + 4) hoff = first;
+                        nent += __popc(m1) + __popc(m2);
+                    }
+                    __syncwarp();
+                    if (TL) {
+                        block_prefix();   // of the run's starting bitset
+                        for (u32 g0 = 0; g0 < TL; g0 += 32) {
+                            const u32 g = g0 + lane;
+                            // the step of leaf g: the last i < len with loff_i <= g
+                            u32 i = 0;
+                            for (u32 stp = 16; stp; stp >>= 1) {
+                                const u32 cand = i + stp;
+                                const u32 v = __shfl_sync(0xffffffffu, loff, cand & 31);
+                                if (cand < len && v <= g) i = cand;
+                            }
+                            const u32 ji = __shfl_sync(0xffffffffu, j0, i);
+                            const u32 li = __shfl_sync(0xffffffffu, loff, i);
+                            const u32 hi = __shfl_sync(0xffffffffu, hoff, i);
+                            const u32 t = t0 + i, b = bb + t;
+                            const u32 fl = st[t].flags;
+                            const u64 xp = st[t].xp;
+                            u32 info = 0, m32 = 0, gpf = 0;
+                            u64 v = 0;
+                            if (g < TL) {
+                                const u32 idx = ji + (g - li);
+                                if (fl & 1u) {
+                                    info = ~0u;   // a prime: lpf = itself, mu = -1
+                                    m32 = A.primes[idx];
+                                    v = A.primes_rcp[idx];
+                                } else {
+                                    const u32 li2 = (fl >> 2) & 7u;
+                                    info = lst_info[li2][idx];
+                                    m32 = lst_m[li2][idx];
+                                    v = lst_rcp[li2][idx];
+                                    gpf = A.trunc ? lst_gpf[li2][idx] : 0;
+                                }
+                            }
+                            const bool valid = m32 && (info >> 1) > b && !(A.trunc && gpf > A.a);
+                            const u32 e = seg_count_end(div_rcp(xp, m32, v), Lw);
+                            u32 below = 0;   // hits of the run's earlier steps below the count end
+                            for (u32 k = 0; k < hi; k++) below += lg[k] < e ? 1u : 0u;
+                            const u32 cnt_u = count_to(e) - below;
+                            const i64 sg = valid ? ((info & 1u) ? 1 : -1) : 0;
+                            acc += sg * (i64)cnt_u;
+                            if (valid) atomicAdd(&tw[t * nw + w], (i32)sg);
+                            nleaves += valid;
+                        }
+                        __syncwarp();
+                    }
+                    // clear the logged bits; counts after every step of the run
+                    for (u32 k = lane; k < nent; k += 32) {
+                        const u32 pos = lg[k];
+                        atomicAnd(&my[pos >> 5], ~(1u << (pos & 31)));
+                        atomicSub(&myblk32[pos >> 9], 1u << (16 * ((pos >> 8) & 1)));
+                    }
+                    const u32 hnext = __shfl_down_sync(0xffffffffu, hoff, 1);
+                    if (lane < len) cw[(t0 + lane) * nw + w] = cnt - (lane + 1 < len ? hnext : nent);
+                    cnt -= nent;
+                    __syncwarp();
+                    t0 += len;
+                }
+            };
             const u32 cnt0 = cnt;
-            for (u64 todo = busy; todo;) {
+            for (u64 todo = busy & lomask; todo;) {
                 const u32 t = __ffsll((long long)todo) - 1;
                 if ((grp >> t) & 1u) {
                     // the run ends below the next busy step that is not in grp
@@ -444,41 +645,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                     if ((leafy >> t) & 1u) {
                         u32 j0, j1;
                         leaf_bounds(t, j0, j1);
-                        {   // prefix counts of the 256-bit blocks of the sub-range
-                            if (bpl == 8) {   // one 16-byte load and store per lane
-                                const uint4 q = ((const uint4*)myblk)[lane];
-                                const u32 c01 = (q.x & 0xFFFFu) + (q.x >> 16), c23 = (q.y & 0xFFFFu) + (q.y >> 16);
-                                const u32 c45 = (q.z & 0xFFFFu) + (q.z >> 16), c67 = (q.w & 0xFFFFu) + (q.w >> 16);
-                                const u32 own = c01 + c23 + c45 + c67;
-                                u32 incl = own;
-                                for (int o = 1; o < 32; o <<= 1) {
-                                    u32 v = __shfl_up_sync(0xffffffffu, incl, o);
-                                    if (lane >= o) incl += v;
-                                }
-                                const u32 r0 = incl - own, r2 = r0 + c01, r4 = r2 + c23, r6 = r4 + c45;
-                                uint4 o4;
-                                o4.x = r0 | ((r0 + (q.x & 0xFFFFu)) << 16);
-                                o4.y = r2 | ((r2 + (q.y & 0xFFFFu)) << 16);
-                                o4.z = r4 | ((r4 + (q.z & 0xFFFFu)) << 16);
-                                o4.w = r6 | ((r6 + (q.w & 0xFFFFu)) << 16);
-                                ((uint4*)mypre)[lane] = o4;
-                            } else {
-                                u32 run = 0;
-                                for (u32 k = 0; k < bpl; k++) run += myblk[lane * bpl + k];
-                                u32 incl = run;
-                                for (int o = 1; o < 32; o <<= 1) {
-                                    u32 v = __shfl_up_sync(0xffffffffu, incl, o);
-                                    if (lane >= o) incl += v;
-                                }
-                                run = incl - run;
-                                for (u32 k = 0; k < bpl; k++) {
-                                    const u32 bi = lane * bpl + k;
-                                    mypre[bi] = (u16)run;
-                                    run += myblk[bi];
-                                }
-                            }
-                            __syncwarp();
-                        }
+                        block_prefix();
                         const u64 xp = st[t].xp;
                         auto one_leaf = [&](u32 info, u32 m32, u64 v, u32 gpf) {
                             // no early exit: a lane without a leaf of b (no entry, lpf <= p_b, or
@@ -487,31 +654,14 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                             const bool valid = m32 && (info >> 1) > b && !(A.trunc && gpf > A.a);
                             const bool neg = info & 1u;
                             const u64 u = div_rcp(xp, m32, v);
-                            const u32 e = seg_count_end(u, Lw);
-                            u32 bi = e >> 8;
-                            if (bi >= nbw) bi = nbw - 1;
-                            // set bits of block bi below the end (0..256 of them): both halves
-                            // of the block at once, no data-dependent loop.  Word i keeps its
-                            // bits below rem - 64 i by a left shift of 64 (i + 1) - rem, taken
-                            // as at least 0; PTX clamps a 64-bit shift above 64 to 64 (result 0).
-                            const u32 rem = e - (bi << 8);
-                            const ulonglong2 h0 = ((const ulonglong2*)my64)[2 * bi];
-                            const ulonglong2 h1 = ((const ulonglong2*)my64)[2 * bi + 1];
-                            auto part = [&](u64 wv, u32 i) -> u32 {
-                                i32 sh = (i32)(64 * i + 64) - (i32)rem;
-                                sh = sh < 0 ? 0 : (sh > 64 ? 64 : sh);
-                                u64 r;
-                                asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(wv), "r"(sh));
-                                return __popcll(r);
-                            };
-                            const u32 c = mypre[bi] + part(h0.x, 0) + part(h0.y, 1) + part(h1.x, 2) + part(h1.y, 3);
+                            const u32 c = count_to(seg_count_end(u, Lw));
                             const i64 sg = valid ? (neg ? 1 : -1) : 0;
                             acc += sg * (i64)c;
                             tl += (int)sg;
                             nleaves += valid;
                         };
                         one_leaf(pf_info, pf_m, pf_v, pf_gpf);                        // first 32, loaded ahead
-                        const u64 later = leafy & ~((2ull << t) - 1);
+                        const u64 later = leafy & lomask & ~((2ull << t) - 1);
                         if (later) prefetch(__ffsll((long long)later) - 1);           // next leaf step
                         for (u32 base = j0 + 32; base < j1; base += 32) {             // the rest, loaded now
                             const u32 i = base + lane;
@@ -625,7 +775,8 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 if (lane == 0) cw[t * nw + w] = cnt;
                 __syncwarp();
             }
-            for (u32 t = lane; t < nb; t += 32) {
+            if (t_sp < nb) sparse_runs(t_sp);
+            for (u32 t = lane; t < t_sp; t += 32) {
                 if ((busy >> t) & 1u) continue;
                 const u64 before = busy & ((1ull << t) - 1);
                 cw[t * nw + w] = before ? cw[(63 - __clzll((long long)before)) * nw + w] : cnt0;
@@ -1006,7 +1157,7 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     static_assert(sizeof(StepInfo) % 16 == 0, "StepInfo must keep 16-byte alignment");
     const size_t smem = BATCH * sizeof(StepInfo) + A.seg_bytes + (size_t)A.nw * (A.sub_bytes >> 5) * 4 +
                         (size_t)BATCH * (A.nw + 1) * 4 + 3 * (size_t)BATCH * A.nw * 4 +
-                        (size_t)BATCH * A.nw;
+                        (size_t)BATCH * A.nw + (size_t)A.nw * LOG_CAP * sizeof(u16);
     // the instantiation: the most resident warps (registers and shared memory
     // permitting), or at least ctas_per_sm resident CTAs when that is set
     struct Variant {
