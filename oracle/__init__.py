@@ -48,6 +48,7 @@ def _load():
                 ("orc_leaf_sums", ctypes.c_int, [u64, u64, ctypes.c_uint32, u64, p_i64]),
                 ("orc_list_leaves", i64, [u64, u64, ctypes.c_uint32, u64, p_i64, i64]),
                 ("orc_nth_prime", u64, [u64]),
+                ("orc_s2_hard_range", ctypes.c_int, [u64, u64, ctypes.c_uint32, u64, u64, p_i64]),
             ]:
                 f = getattr(lib, name)
                 f.restype = res
@@ -97,6 +98,16 @@ def pi_meissel(x: int, y: int = 0) -> int:
 
 def nth_prime(k: int) -> int:
     return int(_load().orc_nth_prime(k))
+
+
+def s2_hard_range(x: int, y: int, c: int, lo: int, hi: int) -> tuple:
+    """The hard leaves with lo <= u < hi only, as one shard sees them: the range
+    sieved alone, phi(lo - 1, b - 1) from the recursion of Eq. (4.1).
+    Returns (sum, number of leaves)."""
+    out = (ctypes.c_int64 * 3)()
+    if _load().orc_s2_hard_range(x, y, c, lo, hi, out) != 0:
+        raise ValueError("oracle domain error")
+    return _i128(out[0], out[1]), out[2]
 
 
 def leaf_sums(x: int, y: int, c: int, a: int = 0) -> dict:

@@ -513,6 +513,81 @@ int64_t orc_list_leaves(uint64_t x, uint64_t y, uint32_t c, uint64_t a_in,
 }
 
 /* p_k for 1 <= k (the k-th prime), plain sieve. */
+/* The hard leaves with u in [lo, hi) only, the way one shard of the hard-leaf
+ * sum sees them (Section 4): the interval [lo, hi) alone is sieved by
+ * p_1, p_2, ... in order, and phi(u, b-1) of a hard leaf (b, m) is the
+ * starting value phi(lo - 1, b - 1), from the recursion of Eq. (4.1), plus the
+ * integers of [lo, u] still unsieved after p_{b-1}.  Same leaf classes as
+ * orc_leaf_sums, a = pi(y): a leaf is hard unless u < p_b (trivial) or
+ * p_b <= u < min(p_b^2, y) (easy).  The sums over any split of [1, z + 1]
+ * into ranges add up to the S2_hard of orc_leaf_sums.  out[0..1]: the sum
+ * (i128), out[2]: the number of leaves.  Returns 0, or -1 on a domain error. */
+int orc_s2_hard_range(uint64_t x, uint64_t y, uint32_t c, uint64_t lo, uint64_t hi, int64_t *out)
+{
+    if (y < 1 || y > orc_isqrt(x) || c > 7 || lo < 1 || hi < lo) return -1;
+    const uint64_t z = x / y;
+    if (hi > z + 1) hi = z + 1;
+    if (lo > hi) lo = hi;
+    uint64_t lim = y;
+    if (orc_isqrt(x) > lim) lim = orc_isqrt(x);
+    if (lim < 32) lim = 32;
+    uint64_t np;
+    uint64_t *P = prime_list(lim, &np);
+    uint64_t a = 0;
+    while (a < np && P[a + 1] <= y) a++;
+    if (c > a) { free(P); return -1; }
+    uint32_t *lpf = (uint32_t *)calloc(y + 1, sizeof(uint32_t));
+    for (uint64_t k = 1; k <= np && P[k] <= y; k++)
+        for (uint64_t q = P[k]; q <= y; q += P[k])
+            if (!lpf[q]) lpf[q] = (uint32_t)k;
+    int8_t *mu = (int8_t *)malloc(y + 1);
+    mu[1] = 1;
+    for (uint64_t n = 2; n <= y; n++) {
+        uint64_t p = P[lpf[n]], r = n / p;
+        mu[n] = (r % p == 0) ? 0 : (int8_t)(-mu[r]);
+    }
+    /* bit v - lo of the bitset stands for the integer v, lo <= v < hi */
+    const uint64_t n = hi - lo;
+    bitcount t;
+    t.nw = n / 64 + 1;
+    t.bits = (uint64_t *)malloc(t.nw * sizeof(uint64_t));
+    t.fw = (int64_t *)calloc(t.nw + 1, sizeof(int64_t));
+    for (uint64_t w = 0; w < t.nw; w++) t.bits[w] = ~0ull;
+    for (uint64_t v = n; v < t.nw * 64; v++) t.bits[v >> 6] &= ~(1ull << (v & 63));
+    for (uint64_t w = 0; w < t.nw; w++) bc_add(&t, w, __builtin_popcountll(t.bits[w]));
+    phi_ctx pc;
+    uint64_t L = orc_isqrt(lo) + 1;   /* pi table of the recursion's Legendre cut-off */
+    if (L < (1u << 16)) L = 1u << 16;
+    if (L > (1u << 26)) L = 1u << 26;
+    phi_ctx_init(&pc, a, L);
+    i128 hard = 0;
+    int64_t nhard = 0;
+    for (uint64_t b = 1; b <= a && n > 0; b++) {
+        const uint64_t p = P[b];
+        if (b > c) {
+            int64_t start = -1;   /* phi(lo - 1, b - 1), computed when a leaf needs it */
+            for (uint64_t m = y / p + 1; m <= y; m++) {
+                if (mu[m] == 0 || lpf[m] <= b) continue;
+                const uint64_t u = (x / p) / m;
+                if (u < lo || u >= hi) continue;
+                if (u < p || ((u128)u < (u128)p * p && u < y)) continue;   /* trivial or easy */
+                if (start < 0) start = phi_rec(&pc, lo - 1, b - 1);
+                hard -= (i128)mu[m] * (start + bc_prefix(&t, u - lo));
+                nhard++;
+            }
+        }
+        /* sieve p_b (itself included) out of [lo, hi) */
+        uint64_t q = lo <= p ? p : ((lo + p - 1) / p) * p;
+        for (; q < hi; q += p) bc_clear(&t, q - lo);
+    }
+    phi_ctx_free(&pc);
+    free(t.bits); free(t.fw);
+    free(lpf); free(mu); free(P);
+    put128(out, hard);
+    out[2] = nhard;
+    return 0;
+}
+
 uint64_t orc_nth_prime(uint64_t k)
 {
     uint64_t lim = 64, np;

@@ -102,6 +102,19 @@ def test_nth_prime_table1(pi_pow10):
         assert o.nth_prime(k) <= 10 ** n < o.nth_prime(k + 1), n
 
 
+def test_s2_hard_range_splits_add_up():
+    # a shard's hard leaves (its range sieved alone, carries from the recursion of
+    # Eq. (4.1)) over any split of [1, z] add up to the whole S2_hard and leaf count
+    rng = random.Random(3)
+    for x, y, c in [(10 ** 9, 1000, 5), (10 ** 10, 4308, 5), (10 ** 10, 2154, 3), (3 * 10 ** 9, 1442 * 3, 7)]:
+        whole = o.leaf_sums(x, y, c)
+        z = x // y
+        cuts = sorted({1, z + 1, *[rng.randrange(2, z) for _ in range(5)]})
+        parts = [o.s2_hard_range(x, y, c, lo, hi) for lo, hi in zip(cuts[:-1], cuts[1:])]
+        assert sum(p[0] for p in parts) == whole["S2_hard"], (x, y, c)
+        assert sum(p[1] for p in parts) == whole["n_hard"], (x, y, c)
+
+
 def test_phi_brute_definition_small():
     # direct gcd count against the definition of phi(x, a) (Section 3)
     for x in range(0, 400, 7):

@@ -1,4 +1,8 @@
-"""The hard-leaf work planner's buffer bound, on CPU.
+"""The arithmetic of the hard-leaf work planner's buffer bound, on CPU.
+
+This checks the formula, restated here in Python, not the kernel: the
+planner's own output (its item count on real and skewed inputs) is checked on
+the GPU by tests/test_gpu_parity.py::test_planner_item_bound.
 
 The planner (pc_hard.cu, plan_split_kernel) splits a segment whose estimated
 leaves e outweigh both its sieve cost b and a fair share of the launch,
