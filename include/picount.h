@@ -85,12 +85,21 @@ typedef struct pc_stats {
     uint64_t hard_leaves;   /* hard special leaves resolved by the sieve */
     uint64_t clears;        /* multiples crossed off by the hard-leaf sieve */
     uint64_t work_items;    /* sieve work items (segments, heavy ones split into replicas) */
-    uint64_t item_steps;    /* (work item, prime) steps actually run, replicas included */
+    uint64_t item_steps;    /* (work item, prime) steps the work items own: every (segment,
+                               prime) step once, heavy segments split among replicas */
     uint64_t kernel_launches;
     double ms_tables, ms_s1, ms_trivial, ms_easy, ms_hard, ms_p2, ms_total;
     double ms_hard_sieve;   /* the segmented sieve kernel alone (CUDA events) */
     uint64_t warp_steps;      /* (warp sub-range, prime) steps with work in the hard-leaf sieve */
     uint64_t leaf_warp_steps; /* of which resolved leaves */
+    double ms_easy_kernel;    /* the easy-leaf kernel alone (CUDA events) */
+    double ms_p2_kernel;      /* the P2 sieve kernel alone (CUDA events) */
+    uint64_t easy_leaves;     /* easy leaves resolved one at a time */
+    uint64_t easy_runs;       /* runs of clustered easy leaves (one pi lookup pair each) */
+    uint64_t easy_run_leaves; /* easy leaves those runs cover */
+    uint64_t p2_clears;       /* multiples crossed off by the P2 sieve */
+    uint64_t presieve_steps;  /* hard-leaf sieve: steps that replicas of heavy segments cross
+                                 off, with no counts, before the steps they own */
 } pc_stats;
 
 typedef struct pc_ctx pc_ctx;

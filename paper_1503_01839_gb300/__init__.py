@@ -51,7 +51,11 @@ class PcStats(ctypes.Structure):
                 ("ms_tables", ctypes.c_double), ("ms_s1", ctypes.c_double), ("ms_trivial", ctypes.c_double),
                 ("ms_easy", ctypes.c_double), ("ms_hard", ctypes.c_double), ("ms_p2", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_hard_sieve", ctypes.c_double),
-                ("warp_steps", ctypes.c_uint64), ("leaf_warp_steps", ctypes.c_uint64)]
+                ("warp_steps", ctypes.c_uint64), ("leaf_warp_steps", ctypes.c_uint64),
+                ("ms_easy_kernel", ctypes.c_double), ("ms_p2_kernel", ctypes.c_double),
+                ("easy_leaves", ctypes.c_uint64), ("easy_runs", ctypes.c_uint64),
+                ("easy_run_leaves", ctypes.c_uint64), ("p2_clears", ctypes.c_uint64),
+                ("presieve_steps", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -138,19 +138,33 @@ static void stats_begin(pc_ctx* ctx, u64 x)
     ctx->stats.x = x;
 }
 
+// Result slots 0..7 hold i128 parts; slots 8..15 (as u64) the call's counters.
 static int result_slots(pc_ctx* ctx, int n, I128Pair** d)
 {
+    (void)n;
     PC_TRY(buf_reserve(ctx, ctx->result, 16 * sizeof(I128Pair)));
-    PC_CUDA(ctx, cudaMemsetAsync(ctx->result.p, 0, n * sizeof(I128Pair), ctx->stream));
+    PC_CUDA(ctx, cudaMemsetAsync(ctx->result.p, 0, 16 * sizeof(I128Pair), ctx->stream));
     *d = ctx->result.as<I128Pair>();
+    ctx->dstat = (unsigned long long*)(ctx->result.as<I128Pair>() + 8);
+    ctx->easy_timed = ctx->p2_timed = false;
     return PC_OK;
 }
 
 static int read_slots(pc_ctx* ctx, int n, i128* out)
 {
     I128Pair h[16];
-    PC_TRY(copy_to_host(ctx, h, ctx->result.p, n * sizeof(I128Pair)));
+    PC_TRY(copy_to_host(ctx, h, ctx->result.p, 16 * sizeof(I128Pair)));
     for (int i = 0; i < n; i++) out[i] = from_pair(h[i]);
+    const u64* c = (const u64*)(h + 8);
+    ctx->stats.easy_leaves += c[0];
+    ctx->stats.easy_runs += c[1];
+    ctx->stats.easy_run_leaves += c[2];
+    ctx->stats.p2_clears += c[3];
+    float ms = 0;
+    if (ctx->easy_timed && cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]) == cudaSuccess) ctx->stats.ms_easy_kernel += ms;
+    if (ctx->p2_timed && cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]) == cudaSuccess) ctx->stats.ms_p2_kernel += ms;
+    ctx->easy_timed = ctx->p2_timed = false;
+    ctx->dstat = nullptr;
     return PC_OK;
 }
 

@@ -120,6 +120,10 @@ struct pc_ctx {
     u32 tuned_alpha[21] = {0};
     u32 tuned_seg[21] = {0};
     u32 seg_call = 0;   // segment bytes chosen for the running pi(x) call (0 = default)
+    // device counters of the running call (easy leaves, runs, their leaves, P2 crossings),
+    // beside the result slots; null outside a leaf-sum call
+    unsigned long long* dstat = nullptr;
+    bool easy_timed = false, p2_timed = false;   // ev[2..3] / ev[4..5] hold kernel times
 };
 
 u32 default_alpha(u64 x);

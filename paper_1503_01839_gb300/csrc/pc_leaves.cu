@@ -240,11 +240,12 @@ __global__ void easy_chunk_map_kernel(u64 nb, const u64* choff, u32* cmap)
 // (a template parameter, so that the default instantiation carries no trace of it)
 template <bool SAMPLED>
 __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u64* choff, const u32* cmap,
-                            u64 nchunks, unsigned long long* queue, I128Pair* part)
+                            u64 nchunks, unsigned long long* queue, I128Pair* part, unsigned long long* stat)
 {
     __shared__ i128 scratch[32];
     const u32 lane = threadIdx.x & 31;
     i64 s = 0;
+    u32 n_one = 0, n_runs = 0, n_run_leaves = 0;   // counters: leaves one at a time, runs, leaves in runs
     // chunks are handed out one at a time to warps (their costs differ widely)
     for (;;) {
         u64 ch = 0;
@@ -311,6 +312,8 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
                                            : (SAMPLED ? pi_sampled(A, bound, &pb) : pi_lookup(A.pit, bound)) - i + 1;
                     }
                     s += (i64)n * ((i64)l - (i64)b + 2);
+                    n_runs++;
+                    n_run_leaves += (u32)n;
                     i += n;
                 }
             }
@@ -348,6 +351,16 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
             }
             const i64 t2 = (i64)piu - (i64)b + 2;
             s += neg ? t2 : -t2;
+            n_one++;
+        }
+    }
+    if (stat) {
+        const u32 a0 = __reduce_add_sync(0xffffffffu, n_one), a1 = __reduce_add_sync(0xffffffffu, n_runs);
+        const u32 a2 = __reduce_add_sync(0xffffffffu, n_run_leaves);
+        if (lane == 0) {
+            if (a0) atomicAdd(stat, (unsigned long long)a0);
+            if (a1) atomicAdd(stat + 1, (unsigned long long)a1);
+            if (a2) atomicAdd(stat + 2, (unsigned long long)a2);
         }
     }
     i128 v = block_sum_i128((i128)s, scratch);
@@ -385,13 +398,16 @@ int run_easy(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     PC_TRY(buf_reserve(ctx, ctx->partials, g * sizeof(I128Pair)));
     PC_TRY(buf_reserve(ctx, ctx->queue, 64));
     PC_CUDA(ctx, cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream));
+    PC_CUDA(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
     if (A.sampled)
         easy_kernel<true><<<g, 256, 0, ctx->stream>>>(A, b_lo, ctx->easy_rng.as<EasyRange>(), choff, ctx->easy_cmap.as<u32>(), nchunks,
-                                            (unsigned long long*)ctx->queue.p, ctx->partials.as<I128Pair>());
+                                            (unsigned long long*)ctx->queue.p, ctx->partials.as<I128Pair>(), ctx->dstat);
     else
         easy_kernel<false><<<g, 256, 0, ctx->stream>>>(A, b_lo, ctx->easy_rng.as<EasyRange>(), choff, ctx->easy_cmap.as<u32>(), nchunks,
-                                            (unsigned long long*)ctx->queue.p, ctx->partials.as<I128Pair>());
+                                            (unsigned long long*)ctx->queue.p, ctx->partials.as<I128Pair>(), ctx->dstat);
     PC_LAUNCHED(ctx);
+    PC_CUDA(ctx, cudaEventRecord(ctx->ev[3], ctx->stream));
+    ctx->easy_timed = true;
     ctx->stats.kernel_launches++;
     return reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out);
 }

@@ -26,6 +26,7 @@ struct P2Args {
     u32* tally;       // number of p answered per segment
     I128Pair* acc;    // sum of local counts per segment
     u32* queue;
+    unsigned long long* stat;   // [3]: multiples crossed off (or null)
 };
 
 // Primes below P2_COOP_P have many wheel rounds per segment and are crossed
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A)
         if (s >= A.nseg) break;
         const u64 L = s * A.span;
         fill_pattern(bits, seg_words, L, patw, A.k0);
+        u32 ncl = 0;
         __syncthreads();
         const u64 end = L + A.span;
         // cross off p_b, k0 < b <= B (the prime itself included)
@@ -67,20 +69,20 @@ __global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A)
             const u64 p = A.primes[b];
             u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[b]) : 0;
             if (ks < p) ks = p;
-            cross_off_coop(bits, A.seg_bytes, L, (u32)p, ks, tid, NT, none);
+            ncl += cross_off_coop(bits, A.seg_bytes, L, (u32)p, ks, tid, NT, none);
         }
         for (u32 task = tid; task < 8 * (A.b_big - A.b_mid); task += NT) {
             const u32 bb = A.b_mid + (task >> 3);
             const u64 p = A.primes[bb];
             u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[bb]) : 0;
             if (ks < p) ks = p;
-            cross_off_class(bits, A.seg_bytes, L, (u32)p, ks, task & 7, none);
+            ncl += cross_off_class(bits, A.seg_bytes, L, (u32)p, ks, task & 7, none);
         }
         for (u32 bb = A.b_big + tid; bb <= A.B; bb += NT) {
             const u64 p = A.primes[bb];
             u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[bb]) : 0;
             if (ks < p) ks = p;
-            cross_off_single(bits, A.seg_bytes, L, (u32)p, ks, none);
+            ncl += cross_off_single(bits, A.seg_bytes, L, (u32)p, ks, none);
         }
         // the sieving primes themselves (only in the first segments)
         for (u32 bb = A.k0 + 1 + tid; bb <= A.B; bb += NT) {
@@ -90,6 +92,10 @@ __global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A)
                 u32 pos = seg_pos(p, L);
                 atomicAnd(&bits[pos >> 5], ~(1u << (pos & 31)));
             }
+        }
+        if (A.stat) {
+            ncl = __reduce_add_sync(0xffffffffu, ncl);
+            if (lane == 0 && ncl) atomicAdd(A.stat + 3, (unsigned long long)ncl);
         }
         __syncthreads();
         for (u32 k = wid; k < nblk; k += NT / 32) {   // a warp per 1024-bit block: no bank conflicts
@@ -287,8 +293,12 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     if (per_sm > 4) per_sm = 4;
     int ctas = ctx->sm_count * per_sm;
     if ((u64)ctas > A.nseg) ctas = (int)A.nseg;
+    A.stat = ctx->dstat;
+    PC_CUDA(ctx, cudaEventRecord(ctx->ev[4], ctx->stream));
     p2_sieve_kernel<512><<<ctas, 512, smem, ctx->stream>>>(A);
     PC_LAUNCHED(ctx);
+    PC_CUDA(ctx, cudaEventRecord(ctx->ev[5], ctx->stream));
+    ctx->p2_timed = true;
     p2_combine_kernel<<<1, 1024, 0, ctx->stream>>>(A, out);
     PC_LAUNCHED(ctx);
     ctx->stats.kernel_launches += 2;

@@ -54,9 +54,10 @@ __device__ __forceinline__ u32 cross_off_coop(u32* bits, u32 seg_bytes, u64 L, u
 
 // One thread crosses off the multiples k*p of one residue class,
 // k = 30 q + R8[j] >= kstart: one per wheel round, p bytes apart.
+// Returns the number of multiples crossed off.
 template <class F>
-__device__ __forceinline__ void cross_off_class(u32* bits, u32 seg_bytes, u64 L, u32 p, u64 kstart, u32 j,
-                                                F&& newly)
+__device__ __forceinline__ u32 cross_off_class(u32* bits, u32 seg_bytes, u64 L, u32 p, u64 kstart, u32 j,
+                                               F&& newly)
 {
     const u32 rj = r8(j);
     u64 q = kstart / 30;
@@ -65,26 +66,30 @@ __device__ __forceinline__ void cross_off_class(u32* bits, u32 seg_bytes, u64 L,
     const u32 bit = idx30(pr % 30);
     const u64 byte64 = (u64)p * q + pr / 30;
     const u64 Lb = L / 30;
-    if (byte64 < Lb) return;               // cannot happen for kstart*p >= L
-    for (u64 by = byte64 - Lb; by < seg_bytes; by += p) {
+    if (byte64 < Lb) return 0;             // cannot happen for kstart*p >= L
+    u32 n = 0;
+    for (u64 by = byte64 - Lb; by < seg_bytes; by += p, n++) {
         const u32 pos = ((u32)by << 3) + bit;
         const u32 mask = 1u << (pos & 31);
         const u32 old = atomicAnd(&bits[pos >> 5], ~mask);
         if (old & mask) newly(pos);
     }
+    return n;
 }
 
 // One thread crosses off all multiples k*p (k >= kstart, k coprime to 30)
-// of a large prime by walking k along the wheel.
+// of a large prime by walking k along the wheel.  Returns their number.
 template <class F>
-__device__ __forceinline__ void cross_off_single(u32* bits, u32 seg_bytes, u64 L, u32 p, u64 kstart,
-                                                 F&& newly)
+__device__ __forceinline__ u32 cross_off_single(u32* bits, u32 seg_bytes, u64 L, u32 p, u64 kstart,
+                                                F&& newly)
 {
     const u64 end = L + 30ull * seg_bytes;
     u64 k = coprime30_at_or_after(kstart);
     u32 r = (u32)(k % 30);
     u64 n = (u64)p * k;
+    u32 cnt = 0;
     while (n < end) {
+        cnt++;
         u32 rel = (u32)(n - L);
         u32 pos = (rel / 30) * 8 + idx30(rel % 30);
         u32 mask = 1u << (pos & 31);
@@ -95,6 +100,7 @@ __device__ __forceinline__ void cross_off_single(u32* bits, u32 seg_bytes, u64 L
         if (r >= 30) r -= 30;
         n += (u64)p * d;
     }
+    return cnt;
 }
 
 // Bit position of the integer n (coprime to 30) in the segment starting at L.

@@ -62,6 +62,28 @@ def test_s2_hard_many_segment_sizes():
             assert cx.s2_hard(x, y, c) == want, (sb, cps, wb)
 
 
+def test_planner_item_bound():
+    # the device planner's work items (segments, heavy ones split into replicas) stay
+    # within the buffer it is given, segments + 8 x resident CTAs + 64, on inputs whose
+    # leaves crowd into a few segments (alpha 1: every special leaf is hard) and on
+    # ordinary ones; the results stay exact
+    import torch
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    for x, alpha, sb in [(10 ** 12, 1, 1024), (10 ** 12, 1, 32768), (10 ** 11, 6, 4096), (10 ** 14, 1, 131072),
+                         (10 ** 10, 1, 1024)]:
+        y = y_for(x, alpha)
+        want = o.leaf_sums(x, y, 5)["S2_hard"] if x <= 10 ** 12 else None
+        with pc.Context(0, seg_bytes=sb) as cx:
+            got = cx.s2_hard(x, y, 5)
+            st = cx.stats()
+        if want is not None:
+            assert got == want, (x, alpha, sb)
+        assert 1 <= st["work_items"] <= st["segments"] + 8 * 8 * n_sm + 64, (x, alpha, sb, st)
+        # every (segment, prime) step belongs to exactly one item (the step count also
+        # holds one wheel-count row entry per segment)
+        assert st["item_steps"] + st["segments"] >= st["steps"]
+
+
 def test_truncated_phi_parts(ctx_small):
     # phi(x, a) = S1 + S2 with the tree truncated at p_a (gpf(m) <= p_a)
     for x, y, a, c in [(10 ** 7, 300, 30, 5), (10 ** 9, 1000, 100, 5), (10 ** 9, 1000, 168, 3),
