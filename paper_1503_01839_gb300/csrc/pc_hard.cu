@@ -48,14 +48,22 @@ static_assert(GROUP_P >= RECOUNT_P, "grouped steps keep their block counters up 
 static constexpr u32 MAX_NW = 16;       // warps (sub-ranges) per segment
 static constexpr u32 MAX_SUB = 8192;    // bytes per sub-range: up to 256 blocks of 256 bits
 static constexpr u32 MAX_SEG = 131072;  // bytes per segment
-// Steps of primes p >= sub-range bytes (at most one multiple per residue class in a
-// sub-range) with p^3 above the segment are taken in runs (sparse_runs below):
-static constexpr u32 RUN_LEAVES = 32;   // a run ends after the step that brings its leaves to this many
-static constexpr u32 LOG_CAP = 32 * 9;  // hit log entries per warp: 32 steps x (8 classes + p itself)
+// Steps of primes p >= sub-range bytes >> RUN_SHIFT (at most 2^RUN_SHIFT multiples per
+// residue class in a sub-range) with p^3 above the segment are taken in runs (sparse_runs):
+// (runs of 32 steps with up to 512 leaves measured fastest on GB300, against 32 to 256
+// leaves and thresholds of 1, 1/4 and 1/8 of the sub-range)
+static constexpr u32 RUN_SHIFT = 1;
+static constexpr u32 RUN_LEAVES = 512;             // a run ends after the step that brings its leaves to this many
+static constexpr u32 LOG_CAP = 512;                // hit log entries per warp (a run's crossings are bounded by it)
 
+// A work item: the steps b_lo <= b < b_hi (and b <= B_s) of segment s.  A light
+// segment is one item with all its steps; a heavy one is split into replicas that
+// each own a run of consecutive steps (see plan_bsplit_kernel).
 struct HardItem {
-    u32 s;    // segment
-    u32 rR;   // replica r << 16 | replica count R
+    u32 s;      // segment
+    u32 b_lo;   // first step
+    u32 b_hi;   // one past the last step (~0: to the segment's last)
+    u32 pad;
 };
 
 struct HardArgs {
@@ -104,10 +112,11 @@ struct __align__(16) StepInfo {
     u8 cbit[8];    // bit of class j inside its byte
     u32 flags;     // bit 0: leaves are primes, bit 1: step has leaves, bits 2-4: m-list (0 = all, k = sub-list k-1),
                    // bit 5: p >= GROUP_P and p^3 > the last integer of the segment (see group_cross),
-                   // bit 6: bit 5 and p >= the sub-range's bytes (see sparse_runs)
+                   // bit 6: bit 5 and p >= the sub-range's bytes >> RUN_SHIFT (see sparse_runs)
     u32 pself;     // segment bit of p_b itself, or ~0
     u32 row;       // off[b - k0]: start of the count / tally rows of b
-    u32 pad[3];
+    u32 runcap;    // bit 6: bound of the step's log entries, 8 ceil(sub_bytes / p) + 1
+    u32 pad[2];
 };
 
 // leaf range of prime b in the segment [L, L + span): m in (mlo, mhi].
@@ -179,6 +188,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
     u32* myblk32 = (u32*)myblk;
     u16* mypre = pre + w * nbw;
     u16* lg = hitlog + w * LOG_CAP;
+
     // count the set bits of every 256-bit block of the sub-range into myblk;
     // returns this lane's share of the total.  Lanes read consecutive 16-byte
     // halves of blocks (no bank conflicts) and pairs of lanes add up a block.
@@ -205,8 +215,8 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
         if (item >= *A.nitems) break;
         const HardItem it = A.items[item];
         const u64 s = it.s;
-        const u32 rep = it.rR >> 16, R = it.rR & 0xFFFFu;
         const u32 Bs = A.segB[s];
+        const u32 b_first = it.b_lo, b_last = it.b_hi - 1 < Bs ? it.b_hi - 1 : Bs;   // this item's steps
         const u64 L = s * A.span;
         const u64 Lw = L + w * A.dspan;
 
@@ -215,18 +225,48 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
             const u64 Lk = L + tid * A.dspan;
             rLk[tid] = Lk ? ~0ull / Lk : 0;
         }
+        if (b_first > A.k0 + 1 && b_first <= b_last) {
+            // A replica that starts at step b_first needs the state after p_{b_first - 1}:
+            // the primes before it are crossed off in any order, with no counts (the
+            // replica that owns those steps records them), then the blocks are counted.
+            __syncthreads();
+            auto none = [](u32) {};
+            u32 b = A.k0 + 1;
+            for (; b < b_first; b++) {   // small primes: the whole CTA, lanes over wheel rounds
+                const u32 p = A.primes[b];
+                if (p >= 512) break;
+                u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[b]) : 0;
+                if (ks < p) ks = p;
+                cross_off_coop(bits, A.seg_bytes, L, p, ks, tid, NT, none);
+            }
+            for (u32 task = tid; task < 8 * (b_first - b); task += NT) {   // one thread per (prime, class)
+                const u32 bq = b + (task >> 3);
+                const u64 p = A.primes[bq];
+                u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[bq]) : 0;
+                if (ks < p) ks = p;
+                cross_off_class(bits, A.seg_bytes, L, (u32)p, ks, task & 7, none);
+            }
+            for (u32 bq = A.k0 + 1 + tid; bq < b_first; bq += NT) {   // the primes themselves (first segment)
+                const u64 p = A.primes[bq];
+                if (p >= L + A.span) break;
+                if (p >= L) {
+                    const u32 pos = seg_pos(p, L);
+                    atomicAnd(&bits[pos >> 5], ~(1u << (pos & 31)));
+                }
+            }
+        }
         __syncthreads();
         u32 cnt = __reduce_add_sync(0xffffffffu, count_blocks());
         if (lane == 0) prev[w] = cnt;
         __syncthreads();
-        if (tid == 0 && rep == 0) {
+        if (tid == 0 && b_first == A.k0 + 1) {
             u32 t = 0;
             for (u32 k = 0; k < nw; k++) t += prev[k];
             A.counts[A.off[0] + (s - A.s0)] = t;
         }
 
-        for (u32 bb = A.k0 + 1; bb <= Bs; bb += BATCH) {
-            const u32 nb = Bs - bb + 1 < BATCH ? Bs - bb + 1 : BATCH;
+        for (u32 bb = b_first; bb <= b_last; bb += BATCH) {
+            const u32 nb = b_last - bb + 1 < BATCH ? b_last - bb + 1 : BATCH;
             __syncthreads();
             // A: per-prime data of the batch
             for (u32 t = tid; t < nb; t += NT) {
@@ -240,7 +280,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 si.q = div_rcp(L, p, vp);
                 si.r0 = (u32)(L - si.q * p);
                 si.row = (u32)A.off[b - A.k0];
-                si.pad[0] = si.pad[1] = si.pad[2] = 0;
+                si.runcap = si.pad[0] = si.pad[1] = 0;
                 si.flags = 0;
                 si.mlo = si.mhi = 0;
                 si.pself = (p >= L && p < L + A.span) ? seg_pos(p, L) : ~0u;
@@ -251,7 +291,13 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         if (A.slK[k] <= b) li = k + 1;
                     si.flags = 2u | (p * p > A.y ? 1u : 0u) | (li << 2);
                 }
-                if (p >= GROUP_P && p * p > div_rcp(L + A.span - 1, p, vp)) si.flags |= p >= A.sub_bytes ? 96u : 32u;
+                if (p >= GROUP_P && p * p > div_rcp(L + A.span - 1, p, vp)) {
+                    si.flags |= 32u;
+                    if (p >= (A.sub_bytes >> RUN_SHIFT)) {
+                        si.flags |= 64u;
+                        si.runcap = 8 * ((A.sub_bytes + (u32)p - 1) / (u32)p) + 1;
+                    }
+                }
                 for (int j = 0; j < 8; j++) {
                     const u32 pr = (u32)p * r8(j);
                     si.coff[j] = pr / 30;
@@ -311,12 +357,6 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
             auto leaf_range = [&](u32 t, u32& j0, u32& j1) {
                 j0 = I[t * (nw + 1) + w + 1];
                 j1 = I[t * (nw + 1) + w];
-                if (R > 1 && j1 > j0) {
-                    const u32 n = j1 - j0, chunk = (n + R - 1) / R;
-                    const u32 a0 = j0 + min(n, rep * chunk), a1 = j0 + min(n, (rep + 1) * chunk);
-                    j0 = a0;
-                    j1 = a1;
-                }
             };
             u64 busy = 0, leafy = 0, grp = 0, sparse = 0;
             u32 lj0[BATCH / 32], lj1[BATCH / 32];   // leaf range of step h*32 + lane
@@ -490,18 +530,19 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 }
                 __syncwarp();
             };
-            // Runs of sparse steps (p >= the sub-range's bytes, so each residue class has at
-            // most one multiple in the sub-range, and p^3 above the segment's last integer).
-            // As in group_cross, a bit still set when the run starts is reached by exactly one
-            // crossing of the run, that of its least prime factor, so every crossing of every
-            // step of the run is found against the bitset as it is at the run's start, in
-            // parallel: lane = (step, residue class), four steps per pass.  The crossings that
-            // hit a set bit go to a log, ordered by step.  A leaf of step t needs the count of
-            // set bits up to u after the steps before t; that is the count on the run's starting
-            // bitset less the logged hits of the run's steps before t below u.  So the leaves of
-            // all steps of a run share 32-lane passes, one block prefix serves the whole run, and
-            // the logged bits are cleared once at its end.  A run ends after the step that
-            // brings its leaves to RUN_LEAVES (or at 32 steps), which keeps the log scans short.
+            // Runs of sparse steps (p >= the sub-range's bytes >> RUN_SHIFT, so each residue
+            // class has at most 2^RUN_SHIFT multiples in the sub-range, and p^3 above the
+            // segment's last integer).  As in group_cross, a bit still set when the run starts
+            // is reached by exactly one crossing of the run, that of its least prime factor, so
+            // every crossing of every step of the run is found against the bitset as it is at
+            // the run's start, in parallel: lane = (step, residue class), four steps per pass.
+            // The crossings that hit a set bit go to a log, ordered by step.  A leaf of step t
+            // needs the count of set bits up to u after the steps before t; that is the count on
+            // the run's starting bitset less the logged hits of the run's steps before t below
+            // u.  So the leaves of all steps of a run share 32-lane passes, one block prefix
+            // serves the whole run, and the logged bits are cleared once at its end.  A run ends
+            // after the step that brings its leaves to RUN_LEAVES, at 32 steps, or where the
+            // log could overflow, which keeps the log scans short.
             auto sparse_runs = [&](u32 t0) {
                 while (t0 < nb) {
                     // the leaf ranges of the next (up to) 32 steps, one per lane
@@ -522,45 +563,56 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                         const u32 v = __shfl_up_sync(0xffffffffu, incl, o);
                         if (lane >= o) incl += v;
                     }
-                    const u32 avail = nb - t0 < 32 ? nb - t0 : 32;
+                    u32 cap = ts < nb ? st[ts].runcap : 0;   // log entries the step may add
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const u32 v = __shfl_up_sync(0xffffffffu, cap, o);
+                        if (lane >= o) cap += v;
+                    }
+                    u32 avail = nb - t0 < 32 ? nb - t0 : 32;
+                    const u32 fits = __popc(__ballot_sync(0xffffffffu, lane < avail && cap <= LOG_CAP));
+                    if (fits < avail) avail = fits;   // at least 1: a step adds at most 8 * 2^RUN_SHIFT + 1
                     const u32 enough = __ballot_sync(0xffffffffu, lane < avail && incl >= RUN_LEAVES);
                     const u32 len = enough ? (u32)__ffs(enough) : avail;   // steps t0 .. t0 + len - 1
                     const u32 TL = __shfl_sync(0xffffffffu, incl, len - 1);
                     const u32 loff = incl - n;                             // first leaf of step t0 + lane
-                    // crossings against the starting bitset; hits logged in step order
+                    // crossings against the starting bitset; hits logged in step order: each lane
+                    // counts its hits, a warp scan gives its log offset, then it writes them
                     u32 nent = 0, hoff = 0;                                // hoff: log entries before step t0 + lane
                     for (u32 c = 0; c < len; c += 4) {
                         const u32 sl = lane >> 3, j = lane & 7, i = c + sl, t = t0 + i;
-                        u32 h = 0, pa = 0, pb = 0;
+                        i32 by = (i32)sub_bytes, p = 0;
+                        u32 bj = 0, pp = ~0u;
                         if (i < len && bb + t < Bs) {
-                            const i32 p = (i32)st[t].p;
-                            const i32 by = basew[t * nw + w] + (i32)st[t].coff[j] + (r8(j) < kmodw[t * nw + w] ? p : 0);
-                            if (by < (i32)sub_bytes) {
-                                const u32 pos = ((u32)by << 3) + st[t].cbit[j];
-                                nclears++;
-                                if ((my[pos >> 5] >> (pos & 31)) & 1u) {
-                                    pa = pos;
-                                    h = 1;
-                                }
-                            }
+                            p = (i32)st[t].p;
+                            by = basew[t * nw + w] + (i32)st[t].coff[j] + (r8(j) < kmodw[t * nw + w] ? p : 0);
+                            bj = st[t].cbit[j];
                             const u32 ps = st[t].pself;
-                            if (j == 0 && ps != ~0u && (ps >> A.sub_shift) == w) {   // p itself
-                                const u32 pos = ps & (sub_bits - 1);
-                                if ((my[pos >> 5] >> (pos & 31)) & 1u) {
-                                    if (h) pb = pos; else pa = pos;
-                                    h++;
-                                }
-                            }
+                            if (j == 0 && ps != ~0u && (ps >> A.sub_shift) == w) pp = ps & (sub_bits - 1);   // p itself
                         }
-                        const u32 m1 = __ballot_sync(0xffffffffu, h >= 1), m2 = __ballot_sync(0xffffffffu, h >= 2);
-                        const u32 below = (1u << lane) - 1u;
-                        const u32 off = nent + __popc(m1 & below) + __popc(m2 & below);
-                        if (h >= 1) lg[off] = (u16)pa;
-                        if (h >= 2) lg[off + 1] = (u16)pb;
+                        u32 h = 0;
+                        for (i32 q = by; q < (i32)sub_bytes; q += p) {
+                            const u32 pos = ((u32)q << 3) + bj;
+                            h += (my[pos >> 5] >> (pos & 31)) & 1u;
+                            nclears++;
+                        }
+                        if (pp != ~0u) h += (my[pp >> 5] >> (pp & 31)) & 1u;
+                        u32 hin = h;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const u32 v = __shfl_up_sync(0xffffffffu, hin, o);
+                            if (lane >= o) hin += v;
+                        }
+                        u32 off = nent + hin - h;
                         // step c + s starts at the entry offset of lane 8 s
                         const u32 first = __shfl_sync(0xffffffffu, off, ((lane - c) & 3) * 8);
                         if (lane >= c && lane < c + 4) hoff = first;
-                        nent += __popc(m1) + __popc(m2);
+                        if (h) {
+                            for (i32 q = by; q < (i32)sub_bytes; q += p) {
+                                const u32 pos = ((u32)q << 3) + bj;
+                                if ((my[pos >> 5] >> (pos & 31)) & 1u) lg[off++] = (u16)pos;
+                            }
+                            if (pp != ~0u && ((my[pp >> 5] >> (pp & 31)) & 1u)) lg[off] = (u16)pp;
+                        }
+                        nent += __shfl_sync(0xffffffffu, hin, 31);
                     }
                     __syncwarp();
                     if (TL) {
@@ -788,7 +840,7 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                 u32 C = 0;
                 for (u32 k = 0; k < nw; k++) C += cw[t * nw + k];
                 const u64 row = st[t].row;
-                if (rep == 0 && b < Bs) A.counts[row + (s - A.s0)] = C;
+                if (b < Bs) A.counts[row + (s - A.s0)] = C;
                 if (b > A.kleaf) {
                     const u32* cp = t ? cw + (t - 1) * nw : prev;
                     i32 T = 0;
@@ -975,6 +1027,15 @@ struct PlanScratch {
     unsigned long long nitems;    // items planned
     u32 cnt[PLAN_BUCKETS];        // items per cost bucket
     u32 cur[PLAN_BUCKETS];        // next free slot of each bucket
+    u32 nheavy;                   // segments split into replicas
+    u32 pad;
+};
+
+struct HeavySeg {
+    u32 s;     // segment
+    u32 pos;   // its first item
+    u32 R;     // its replicas (items pos .. pos + R - 1)
+    u32 pad;
 };
 
 struct PlanArgs {
@@ -988,7 +1049,9 @@ struct PlanArgs {
     PlanScratch* scr;
     u32* split;                 // per segment: R | bucket << 16 (R = 0: no item)
     HardItem* items;
-    unsigned long long* stat;   // [4] items, [5] item steps, [6] set when cap was too small
+    HeavySeg* heavy;            // the segments with R > 1
+    unsigned long long* stat;   // [4] items, [5] item steps, [6] set when cap was too small,
+                                // [7] steps replicas cross off before their own
 };
 
 __device__ __forceinline__ double seg_cost(const PlanArgs& P, u64 s)
@@ -1030,11 +1093,11 @@ __global__ void plan_split_kernel(PlanArgs P)
                 R = (u32)fmin(1024.0, ceil(e / fmax(room, 1.0)));
                 if (R < 1) R = 1;
             }
-            const int k = (int)floor(4.0 * log2(base + e / R));
+            const int k = (int)floor(4.0 * log2((base + e) / R));   // a replica's share
             const u32 key = (u32)(k < 0 ? 0 : (k >= PLAN_BUCKETS ? PLAN_BUCKETS - 1 : k));
             v = R | (key << 16);
             atomicAdd(&P.scr->cnt[key], R);
-            atomicAdd(&P.stat[5], (unsigned long long)R * (P.segB[s] - P.k0));
+            atomicAdd(&P.stat[5], (unsigned long long)(P.segB[s] - P.k0));
         }
         P.split[s] = v;
     }
@@ -1064,7 +1127,86 @@ __global__ void plan_scatter_kernel(PlanArgs P)
         const u32 v = P.split[s], R = v & 0xFFFFu;
         if (!R) continue;
         const u32 pos = atomicAdd(&P.scr->cur[v >> 16], R);
-        for (u32 r = 0; r < R; r++) P.items[pos + r] = HardItem{(u32)s, (r << 16) | R};
+        // replica 0 starts at the first step; the others get their steps in plan_bsplit_kernel
+        for (u32 r = 0; r < R; r++) P.items[pos + r] = HardItem{(u32)s, r ? ~0u : P.k0 + 1, ~0u, 0u};
+        if (R > 1) P.heavy[atomicAdd(&P.scr->nheavy, 1u)] = HeavySeg{(u32)s, pos, R, 0u};
+    }
+}
+
+// Estimated cost of step b of the segment [L, L + span), in the units of seg_cost (one
+// leaf = 1): 128 for the step, 0.08 per crossing, plus its hard leaves (upper bound, as in
+// hard_estimate_kernel).  Integer, so that prefix sums are exact.
+__device__ __forceinline__ unsigned long long step_cost(const HardArgs& A, u32 b, u64 L, u64 vL, u64 vLs)
+{
+    const u64 p = A.primes[b], vp = A.primes_rcp[b];
+    unsigned long long c = 128 + (16ull * A.seg_bytes / p) / 25;
+    if (b > A.kleaf && b <= A.a) {
+        const u64 xp = div_rcp(A.x, p, vp);
+        u64 mlo, mhi;
+        if (leaf_window(A, p, vp, xp, L, vL, vLs, mlo, mhi)) {
+            if (p * p > A.y) {
+                const u64 k0 = pc_min(pc_max(pi_lookup(A.pit, mlo), b), A.a);
+                const u64 k1 = pc_min(pc_max(pi_lookup(A.pit, mhi), b), A.a);
+                c += k1 - k0;
+            } else {
+                c += rank_lookup(A.rk, mhi) - rank_lookup(A.rk, mlo);
+            }
+        }
+    }
+    return c;
+}
+
+// The steps of a heavy segment's replicas: replica r owns the steps from the first b
+// whose cost before it reaches r / R of the segment's total (one CTA per segment; a
+// prefix sum of exact integer costs, so every step goes to exactly one replica).
+__global__ void __launch_bounds__(256) plan_bsplit_kernel(HardArgs A, PlanArgs P)
+{
+    __shared__ unsigned long long wsum[8];
+    __shared__ unsigned long long s_tot;
+    const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (P.stat[6]) return;
+    const u32 nh = P.scr->nheavy;
+    for (u32 h = blockIdx.x; h < nh; h += gridDim.x) {
+        const HeavySeg hs = P.heavy[h];
+        const u64 s = hs.s, L = s * A.span, R = hs.R;
+        const u32 Bs = A.segB[s];
+        const u64 vL = L ? ~0ull / L : 0, vLs = ~0ull / (L + A.span);
+        const u32 nsteps = Bs - A.k0, per = (nsteps + 255) / 256;
+        const u32 b0 = pc_min((u64)A.k0 + 1 + (u64)tid * per, (u64)Bs + 1), b1 = pc_min((u64)b0 + per, (u64)Bs + 1);
+        unsigned long long mine = 0;
+        for (u32 b = b0; b < b1; b++) mine += step_cost(A, b, L, vL, vLs);
+        unsigned long long incl = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long run = 0;
+            for (u32 k = 0; k < 8; k++) {
+                const unsigned long long v = wsum[k];
+                wsum[k] = run;
+                run += v;
+            }
+            s_tot = run;
+        }
+        __syncthreads();
+        const unsigned long long T = s_tot;
+        unsigned long long before = wsum[wid] + incl - mine;
+        for (u32 b = b0; b < b1; b++) {
+            const unsigned long long after = before + step_cost(A, b, L, vL, vLs);
+            // replicas r with R * before < r * T <= R * after start right after step b
+            u64 r_hi = R * after / T;
+            if (r_hi > R - 1) r_hi = R - 1;
+            for (u64 r = R * before / T + 1; r <= r_hi; r++) {
+                P.items[hs.pos + r].b_lo = b + 1;
+                P.items[hs.pos + r - 1].b_hi = b + 1;
+                if (b + 1 <= Bs) atomicAdd(&P.stat[7], (unsigned long long)(b - A.k0));
+            }
+            before = after;
+        }
+        __syncthreads();
     }
 }
 
@@ -1119,13 +1261,15 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 
     const u64 nrows = bmax - A.k0 + 1;
     PC_TRY(buf_reserve(ctx, ctx->seg_b, A.nseg * sizeof(u32) + (nrows + 1) * sizeof(u32)));
-    PC_TRY(buf_reserve(ctx, ctx->seg_off, (nrows + 1) * sizeof(u64) + 3 * A.nseg * sizeof(u64) + A.nseg * sizeof(u32)));
+    PC_TRY(buf_reserve(ctx, ctx->seg_off, (nrows + 1) * sizeof(u64) + 3 * A.nseg * sizeof(u64) + A.nseg * sizeof(u32) +
+                                              A.nseg * sizeof(HeavySeg) + 16));
     u32* segB = ctx->seg_b.as<u32>();
     u32* rowlen = segB + A.nseg;
     u64* off = ctx->seg_off.as<u64>();
     unsigned long long* est = (unsigned long long*)(off + nrows + 1);
     u64* rcp_seg = (u64*)(est + A.nseg);
     u32* split = (u32*)(rcp_seg + 2 * A.nseg);   // the work-item split of every segment
+    HeavySeg* heavy = (HeavySeg*)(((uintptr_t)(split + A.nseg) + 15) & ~(uintptr_t)15);
     A.rcp_seg = rcp_seg;
     A.rcp_y = ~0ull / P.y;
     seg_b_kernel<<<(unsigned)((A.nseg + 255) / 256), 256, 0, ctx->stream>>>(P.x, A.nseg, A.span, A.bmax, A.pit, segB,
@@ -1233,7 +1377,7 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     PC_CUDA(ctx, cudaMemsetAsync(scr, 0, sizeof(PlanScratch), ctx->stream));
     PC_CUDA(ctx, cudaMemsetAsync(ctx->tallies.p, 0, total * sizeof(i32), ctx->stream));
     PlanArgs PA{segB, est, A.k0, (double)P.x, (double)P.z, A.span, A.s0, A.s1, 1.0 / (4.0 * ctas), cap,
-                scr, split, ditems, A.stat};
+                scr, split, ditems, heavy, A.stat};
     const unsigned pg = (unsigned)pc_min((A.s1 - A.s0 + 255) / 256, (u64)ctx->sm_count * 4);
     plan_cost_kernel<<<pg, 256, 0, ctx->stream>>>(PA);
     PC_LAUNCHED(ctx);
@@ -1243,7 +1387,9 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     PC_LAUNCHED(ctx);
     plan_scatter_kernel<<<pg, 256, 0, ctx->stream>>>(PA);
     PC_LAUNCHED(ctx);
-    ctx->stats.kernel_launches += 4;
+    plan_bsplit_kernel<<<ctx->sm_count * 2, 256, 0, ctx->stream>>>(A, PA);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches += 5;
 
     cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
     PC_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
@@ -1260,14 +1406,15 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     PC_TRY(reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out));
     PC_TRY(reduce_i128(ctx, A.acc, ctas, out));
 
-    u64 nl[7] = {0, 0, 0, 0, 0, 0, 0};
-    PC_TRY(copy_to_host(ctx, nl, A.stat, 7 * sizeof(u64)));
+    u64 nl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    PC_TRY(copy_to_host(ctx, nl, A.stat, 8 * sizeof(u64)));
     if (nl[6]) {
         pc_set_error(ctx, "hard-leaf sieve: work items exceed the planned %llu slots", (unsigned long long)cap);
         return PC_EOVERFLOW;
     }
     ctx->stats.work_items = nl[4];
     ctx->stats.item_steps += nl[5];
+    ctx->stats.presieve_steps += nl[7];
     ctx->stats.warp_steps += nl[2];
     ctx->stats.leaf_warp_steps += nl[3];
     float ms = 0;
