@@ -143,6 +143,96 @@ def profile_traffic():
     return rec.get("dram_bytes_per_launch")
 
 
+# Algorithmic unit costs of the roofline models (stated in the design notes).  The
+# hard-leaf sieve: per crossing one 32-bit shared-memory read-modify-write and about 4
+# integer operations; per (segment, prime) step one 64-bit reduction (about 16 integer
+# operations); per hard leaf one 64-by-32 division (about 16) and a count of the set
+# bits below u: the block prefix plus on average half of a 1024-bit block (16 words:
+# 16 bank accesses and about 32 integer operations) -> 17 accesses and 48 operations.
+HARD_SMEM = {"crossing": 1.0, "leaf": 17.0}
+HARD_INT = {"crossing": 4.0, "step": 16.0, "leaf": 48.0}
+# Easy leaves: per leaf resolved alone one reciprocal division (16), the pi record's
+# index and bit (8) and its popcount and sum (8); per run of clustered leaves two of
+# those lookups and one more division (48).  P2: one shared-memory atomic per crossing.
+EASY_INT = {"leaf": 32.0, "run": 48.0}
+P2_SMEM = {"crossing": 1.0}
+
+
+def roofline_term(work, ms, peak_per_s, unit):
+    achieved = work / (ms / 1000.0)
+    return {"work": work, "achieved": achieved / 1e9, "peak": peak_per_s / 1e9, "unit": unit,
+            "frac": achieved / peak_per_s}
+
+
+def ncu_summary(name, sources):
+    """The committed ncu counters of a kernel (profiles/<name>_ncu.json), if they were
+    taken on the current source of the files that define it."""
+    try:
+        with open(os.path.join(ROOT, "profiles", name + "_ncu.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for src in sources:
+        with open(os.path.join(ROOT, "paper_1503_01839_gb300", "csrc", src), "rb") as f:
+            h.update(f.read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec
+
+
+def hard_roofline(st, sieve_ms, n_sm, f_mhz, traffic):
+    """Both terms of the shared-memory / INT32 model of the hard-leaf sieve:
+    t_roof = max(bank accesses / (32 N_SM f), integer ops / (128 N_SM f))."""
+    clears, leaves, steps = float(st["clears"]), float(st["hard_leaves"]), float(st["steps"])
+    f = f_mhz * 1e6
+    smem = roofline_term(HARD_SMEM["crossing"] * clears + HARD_SMEM["leaf"] * leaves, sieve_ms, 32.0 * n_sm * f,
+                         "G smem-bank-accesses/s")
+    smem["per_unit"] = "1 per crossing, 17 per hard leaf"
+    ints = roofline_term(HARD_INT["crossing"] * clears + HARD_INT["step"] * steps + HARD_INT["leaf"] * leaves,
+                         sieve_ms, 128.0 * n_sm * f, "G int32-ops/s")
+    ints["per_unit"] = "4 per crossing, 16 per (segment, prime) step, 48 per hard leaf"
+    top = smem if smem["frac"] >= ints["frac"] else ints
+    out = {"bound": "smem" if top is smem else "alu", "achieved": top["achieved"], "peak": top["peak"],
+           "unit": top["unit"], "frac": top["frac"], "traffic": traffic, "kernel": "hard_sieve_kernel",
+           "kernel_ms": sieve_ms, "terms": {"smem": smem, "int32": ints},
+           "peak_basis": "32 banks / 128 INT32 lanes x %d SMs x %.0f MHz (max SM clock, MEASURED_PEAKS.json)"
+                         % (n_sm, f_mhz)}
+    nc = ncu_summary("hard_sieve_kernel", ("pc_hard.cu", "pc_sieve.cuh", "pc_common.cuh"))
+    if nc:
+        out["ncu"] = {k: nc[k] for k in ("workload", "alu_pipe", "issue_active", "shared_pipe", "warps_active")
+                      if k in nc}
+    return out
+
+
+def other_rooflines(sp, n_sm, f_mhz):
+    """Rooflines of the easy-leaf kernel (INT32) and the P2 sieve (shared-memory
+    atomics) from one pi(x) call's counters and CUDA-event kernel times."""
+    f = f_mhz * 1e6
+    out = {}
+    if sp.get("ms_easy_kernel", 0) > 0:
+        work = EASY_INT["leaf"] * sp["easy_leaves"] + EASY_INT["run"] * sp["easy_runs"]
+        t = roofline_term(work, sp["ms_easy_kernel"], 128.0 * n_sm * f, "G int32-ops/s")
+        t.update({"bound": "alu", "kernel_ms": sp["ms_easy_kernel"], "easy_leaves": sp["easy_leaves"],
+                  "easy_runs": sp["easy_runs"], "easy_run_leaves": sp["easy_run_leaves"],
+                  "per_unit": "32 per leaf resolved alone, 48 per run of clustered leaves"})
+        nc = ncu_summary("easy_kernel", ("pc_leaves.cu", "pc_common.cuh"))
+        if nc:
+            t["ncu"] = {k: nc[k] for k in ("workload", "alu_pipe", "issue_active", "l2_hit", "dram_gbs") if k in nc}
+        out["easy_kernel"] = t
+    if sp.get("ms_p2_kernel", 0) > 0:
+        t = roofline_term(P2_SMEM["crossing"] * sp["p2_clears"], sp["ms_p2_kernel"], 32.0 * n_sm * f,
+                          "G smem-bank-accesses/s")
+        t.update({"bound": "smem", "kernel_ms": sp["ms_p2_kernel"], "crossings": sp["p2_clears"],
+                  "per_unit": "1 shared-memory atomic per crossing"})
+        nc = ncu_summary("p2_sieve_kernel", ("pc_p2.cu", "pc_sieve.cuh", "pc_common.cuh"))
+        if nc:
+            t["ncu"] = {k: nc[k] for k in ("workload", "bank_conflict_frac", "issue_active", "shared_pipe")
+                        if k in nc}
+        out["p2_sieve_kernel"] = t
+    return out
+
+
 def cpu_baseline(seconds_cap=30.0):
     """The oracle (single-threaded C, unchanged) on a bounded sample: the
     same per-leaf sieve of [1, z] at x = 10^12, y = iroot3(x)."""
@@ -160,6 +250,66 @@ def cpu_baseline(seconds_cap=30.0):
     dt = (time.perf_counter() - t0) / n
     return {"value": (x // y) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "oracle per-leaf sieve of [1, z], x=1e12, y=iroot3(x)=10^4, z=1e8, c=5; %d run(s)" % n}
+
+
+def host_cpu():
+    """The host's core count and CPU model (the oracle runs there)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k = k.strip().lower()
+                if k in ("model name", "cpu model", "hardware") and v.strip():
+                    model = v.strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
+
+
+def cpu_oracle_pi(xs=(10 ** 10, 10 ** 12)):
+    """The Meissel-Lehmer oracle (plain phi recursion, one core) on this host:
+    wall time of pi(x) for each x, checked against Table 1."""
+    import oracle
+    oracle.build()
+    table1 = {10 ** 10: 455052511, 10 ** 12: 37607912018}
+    out = {}
+    for x in xs:
+        t0 = time.perf_counter()
+        v = oracle.pi_meissel(x)
+        dt = time.perf_counter() - t0
+        assert v == table1[x], (x, v)
+        out["%.0e" % x] = {"s": dt, "pi": v, "cores": 1}
+    return out
+
+
+def cpu_oracle_batch(n=4096, seed=0, x_max=10 ** 11):
+    """The benchmark batch's queries up to x_max on every host core (spawned
+    workers, one oracle pi(x) each): queries/s, beside the GPU batch figure."""
+    import concurrent.futures as cf
+    import multiprocessing
+    import oracle
+    from paper_1503_01839_gb300 import inputs
+    oracle.build()
+    xs = [x for x in inputs.batch_queries(n, seed) if x <= x_max]
+    cores = os.cpu_count() or 1
+    with cf.ProcessPoolExecutor(cores, mp_context=multiprocessing.get_context("spawn")) as ex:
+        list(ex.map(oracle.iroot3, [8] * cores))            # start the workers outside the timing
+        t0 = time.perf_counter()
+        vals = list(ex.map(oracle.pi_meissel, xs, chunksize=16))
+        dt = time.perf_counter() - t0
+    return {"queries": len(xs), "x": "the batch's queries with x <= %.0e" % x_max, "s": dt,
+            "qps": len(xs) / dt, "cores": cores, "results": vals}
 
 
 def run_reference(args):
@@ -215,6 +365,9 @@ def run_pi_mode(args):
     return 0
 
 
+batch_xs_results = None   # (queries, results) of the last run_batch, for the oracle's check
+
+
 def run_batch(local, n, streams, seed=0):
     """The batched workload: n pi(x) queries, log10 x ~ U(8, 15) (seed 0),
     as one pc_pi_count_batch call, against a host loop of plain pc_pi_count
@@ -237,6 +390,8 @@ def run_batch(local, n, streams, seed=0):
         plain = [cx.pi_count(v) for v in xs]
         tl = time.perf_counter() - t0
     assert got == plain, "batched and plain results differ"
+    global batch_xs_results
+    batch_xs_results = (xs, got)
     return {"queries": n, "x": "floor(10^e), e ~ U(8, 15), numpy default_rng(%d)" % seed, "x_sha256": sha,
             "slots": streams, "batch_s": tb, "batch_qps": n / tb, "plain_loop_s": tl, "plain_qps": n / tl,
             "speedup": tl / tb, "bit_exact": True, "gpu_launches": launches,
@@ -339,6 +494,8 @@ def main():
     ap.add_argument("--batch", type=int, default=4096, help="queries of the batched workload (0: skip)")
     ap.add_argument("--serve", type=int, default=1000, help="requests of the served workload (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-low-rate", type=float, default=150.0,
+                    help="a second, FIFO run offered below capacity, where latency is service time (0: skip)")
     ap.add_argument("--streams", type=int, default=8, help="query slots of the batched/served forms")
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: split one S2_hard into N independent shards instead of N replicas")
@@ -353,6 +510,8 @@ def main():
     if args.mode == "serve":
         for pol in (0, 1):
             print(json.dumps(run_serve(0, args.serve, args.serve_rate, args.streams, policy=pol)), flush=True)
+        if args.serve_low_rate > 0:
+            print(json.dumps(run_serve(0, args.serve, args.serve_low_rate, args.streams, policy=0)), flush=True)
         return 0
     if args.impl == "reference":
         return run_reference(args)
@@ -428,15 +587,9 @@ def main():
     sieve_ms = statistics.mean(s["ms_hard_sieve"] for s in stats)
     launches = sum(int(s["kernel_launches"]) for s in stats)
 
-    # roofline of the sieve kernel: 32-bit shared-memory bank accesses.
-    # per crossing-off: one atomic RMW (1); per hard leaf: the block-prefix
-    # read (1) + on average half of a 1024-bit block of u64 words (16).
     peaks = measured_peaks()
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    accesses = float(st["clears"]) + 17.0 * float(st["hard_leaves"])
-    achieved = accesses / (sieve_ms / 1000.0) / 1e9
-    peak = 32.0 * n_sm * sm_max_mhz * 1e6 / 1e9
     traffic = profile_traffic()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -445,16 +598,14 @@ def main():
             "config": config(int(st["seg_bytes"]), "shards (Section 4 starting values)" if shard else "replicas"),
             "e2e": {"value": job_throughput(z, 1 if shard else world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 24, "d2h_bytes_per_step": 16},
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G smem-bank-accesses/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "hard_sieve_kernel", "kernel_ms": sieve_ms,
-                         "peak_basis": "32 banks x %d SMs x %.0f MHz (max SM clock, MEASURED_PEAKS.json)"
-                                       % (n_sm, sm_max_mhz)},
+            "roofline": hard_roofline(st, sieve_ms, n_sm, sm_max_mhz, traffic),
             "clocks": clk.summary(),
             "s2_hard": str(sum_over_ranks(ref, world) if shard else ref),
             "hard_leaves": int(st["hard_leaves"]), "clears": int(st["clears"]),
             "hard_leaves_per_s": float(st["hard_leaves"]) / (ms_per_step / 1000.0),
             "segments": int(st["segments"]), "steps_seg_prime": int(st["steps"]),
+            "work_items": int(st["work_items"]), "item_steps": int(st["item_steps"]),
+            "warp_steps": int(st["warp_steps"]), "leaf_warp_steps": int(st["leaf_warp_steps"]),
             "timed_wall_s": t_wall}
 
     if rank == 0 and not args.no_pi:
@@ -464,7 +615,7 @@ def main():
             al = 0
             ctx.pi_count(xx, al)
             ts = []
-            for _ in range(3):
+            for _ in range(5):
                 flush.zero_()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -472,17 +623,34 @@ def main():
                 ts.append(time.perf_counter() - t0)
                 assert got == want, (xx, got, want)
             sp = ctx.stats()
-            pis["%.0e" % xx] = {"wall_s": min(ts), "alpha": ctx.tuned(xx)[0], "pi": got, "table1": want,
-                                "y": sp["y"], "timing": "host wall clock around pc_pi_count, best of 3, L2 flushed",
+            pis["%.0e" % xx] = {"wall_s": min(ts), "wall_s_mean": statistics.mean(ts),
+                                "wall_s_stdev": statistics.stdev(ts), "runs": len(ts),
+                                "alpha": ctx.tuned(xx)[0], "pi": got, "table1": want, "y": sp["y"],
+                                "timing": "host wall clock around pc_pi_count, 5 runs (best, mean, stdev), "
+                                          "L2 flushed before each",
                                 "ms": {k: round(sp[k], 3) for k in ("ms_tables", "ms_s1", "ms_trivial",
-                                                                     "ms_easy", "ms_hard", "ms_p2")}}
+                                                                     "ms_easy", "ms_hard", "ms_p2",
+                                                                     "ms_hard_sieve", "ms_easy_kernel",
+                                                                     "ms_p2_kernel")},
+                                "rooflines": other_rooflines(sp, n_sm, sm_max_mhz)}
         line["pi_wall"] = pis
     if rank == 0 and args.batch > 0:
         line["batch"] = run_batch(local, args.batch, args.streams)
     if rank == 0 and args.serve > 0:
         line["served"] = [run_serve(local, args.serve, args.serve_rate, args.streams, policy=pol) for pol in (0, 1)]
+        if args.serve_low_rate > 0:
+            line["served"].append(run_serve(local, args.serve, args.serve_low_rate, args.streams, policy=0))
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"]["host"] = host_cpu()
+        line["cpu_baseline"]["oracle_pi"] = cpu_oracle_pi()
+        if args.batch > 0:
+            ob = cpu_oracle_batch(args.batch)
+            if batch_xs_results:
+                gpu = [v for x, v in zip(*batch_xs_results) if x <= 10 ** 11]
+                ob["bit_exact_with_gpu_batch"] = gpu == ob["results"]
+            del ob["results"]
+            line["cpu_baseline"]["oracle_batch"] = ob
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
