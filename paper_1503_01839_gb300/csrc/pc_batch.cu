@@ -215,6 +215,69 @@ static int run_queries(pc_ctx* ctx, const std::vector<Query>& q, std::vector<u64
     return first_rc.load();
 }
 
+int mq_final(pc_ctx* ctx, const MQPlan& P, u64* d_out, int* d_bad);
+
+// The pi(x) queries of a batch with 2^20 <= x < MQ_MAX as one schedule: every phase
+// (ordinary and trivial leaves, easy leaves, the hard-leaf sieve, P2, the final sums)
+// is one launch over all queries, on the context's stream, after one read-back of
+// the table values every query needs (pi(y), pi(isqrt z), ...).  The queries are
+// sorted largest first, so that the sieve launches start on the longest segments.
+static constexpr u64 MQ_MAX = 10000000000000000ull;   // 1e16: larger ones run one by one
+
+static int multi_batch(pc_ctx* ctx, const std::vector<u64>& xs, std::vector<u64>& out)
+{
+    const u32 n = (u32)xs.size();
+    std::vector<u32> order(n);
+    for (u32 i = 0; i < n; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](u32 i, u32 j) { return xs[i] > xs[j]; });
+    MQPlan P;
+    P.Q = n;
+    P.hq.resize(n);
+    TableNeeds N;
+    for (u32 k = 0; k < n; k++) {
+        const u64 x = xs[order[k]];
+        const u64 r = pc_isqrt(x);
+        u64 y = (u64)choose_alpha(ctx, x) * pc_iroot3(x);
+        if (y > r) y = r;
+        MQ& m = P.hq[k];
+        memset(&m, 0, sizeof(m));
+        m.x = x;
+        m.y = y;
+        m.z = x / y;
+        m.c = 5;   // pi(y) >= 5 for every x >= 2^20
+        needs_pi(ctx, x, N);
+    }
+    PC_TRY(build_needs(ctx, N));
+    // mq_q: queries (n MQ) | parts (5 n I128Pair) | results (n u64) | overflow flag
+    const size_t o_parts = ((size_t)n * sizeof(MQ) + 15) / 16 * 16;
+    const size_t o_out = o_parts + (size_t)n * 5 * sizeof(I128Pair), o_bad = o_out + (size_t)n * 8;
+    PC_TRY(buf_reserve(ctx, ctx->mq_q, o_bad + 16));
+    unsigned char* base = ctx->mq_q.as<unsigned char>();
+    P.dq = (const MQ*)base;
+    P.parts = (I128Pair*)(base + o_parts);
+    u64* d_out = (u64*)(base + o_out);
+    int* d_bad = (int*)(base + o_bad);
+    PC_CUDA(ctx, cudaMemcpyAsync(base, P.hq.data(), n * sizeof(MQ), cudaMemcpyHostToDevice, ctx->stream));
+    PC_CUDA(ctx, cudaMemsetAsync(P.parts, 0, (size_t)n * 5 * sizeof(I128Pair) + (size_t)n * 8 + 16, ctx->stream));
+    PC_TRY(mq_info(ctx, P));   // the batch's one read-back before the leaf sums
+    PC_TRY(mq_s1_trivial(ctx, P));
+    PC_TRY(mq_easy(ctx, P));
+    PC_TRY(mq_hard(ctx, P));
+    PC_TRY(mq_p2(ctx, P));
+    PC_TRY(mq_final(ctx, P, d_out, d_bad));
+    std::vector<u64> res(n);
+    int bad = 0;
+    PC_CUDA(ctx, cudaMemcpyAsync(res.data(), d_out, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    PC_CUDA(ctx, cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    PC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (bad) {
+        pc_set_error(ctx, "batch: pi(x) out of range (internal inconsistency)");
+        return PC_EOVERFLOW;
+    }
+    for (u32 k = 0; k < n; k++) out[order[k]] = res[k];
+    return PC_OK;
+}
+
 extern "C" int pc_pi_count_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint64_t* out, void* stream)
 {
     if (!ctx || (n && (!xs || !out))) return PC_EINVAL;
@@ -229,52 +292,52 @@ extern "C" int pc_pi_count_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint
     } else {
         memcpy(hx.data(), xs, n * sizeof(u64));
     }
-    // Queries up to LOOKUP_MAX, if there are enough of them, are answered from
-    // the pi table itself (one lookup kernel for all); the rest run on the slots.
-    static constexpr u64 LOOKUP_MAX = (1ull << 32) - 1;   // the pi table's own limit: 286 MB
-    static constexpr size_t LOOKUP_MIN_QUERIES = 64;
-    u64 lk = 0;
-    size_t nsmall = 0;
-    for (size_t i = 0; i < n; i++) {
+    for (size_t i = 0; i < n; i++)
         if (hx[i] >> 63) return PC_ERANGE;
-        if (hx[i] <= LOOKUP_MAX) {
-            lk = pc_max(lk, hx[i]);
-            nsmall++;
-        }
-    }
-    const bool lookup = nsmall >= LOOKUP_MIN_QUERIES;
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    // x < 2^20: one pi-table lookup, as pc_pi_count answers them; 2^20 <= x < 1e16: the
+    // batched launches; larger x: one at a time (they fill the GPU on their own)
+    std::vector<u64> sx, mx, bx;
+    std::vector<size_t> si, mi, bi;
     TableNeeds N;
-    if (lookup) N.add(lk, 64, 0, 7);
-    std::vector<Query> q;
-    std::vector<size_t> qi;
-    std::vector<u64> sx;
-    std::vector<size_t> si;
     for (size_t i = 0; i < n; i++) {
         if (hx[i] < 2) {
-            hout[i] = 0;   // pi(0) = pi(1) = 0 (the table marks 1 as a wheel residue)
-        } else if (lookup && hx[i] <= LOOKUP_MAX) {
+            hout[i] = 0;
+        } else if (hx[i] < (1ull << 20)) {
             sx.push_back(hx[i]);
             si.push_back(i);
+            N.add(hx[i], 64, 0, 7);
+        } else if (hx[i] < MQ_MAX && ctx->params.pi_gather == 0) {
+            mx.push_back(hx[i]);
+            mi.push_back(i);
         } else {
-            needs_pi(ctx, hx[i], N);
-            q.push_back(Query{PC_QUERY_PI, hx[i], 0});
-            qi.push_back(i);
+            bx.push_back(hx[i]);
+            bi.push_back(i);
         }
     }
-    PC_TRY(build_needs(ctx, N));
     if (!sx.empty()) {
+        PC_TRY(build_needs(ctx, N));
         std::vector<u64> sv(sx.size());
         PC_TRY(tables_pi_many(ctx, sx.data(), sv.data(), sx.size()));
         for (size_t k = 0; k < sx.size(); k++) hout[si[k]] = sv[k];
+        ctx->stats.kernel_launches++;
     }
-    if (!q.empty()) {
-        std::vector<u64> qv(q.size(), 0);
-        PC_TRY(run_queries(ctx, q, qv));   // sets the batch's counters
-        for (size_t k = 0; k < q.size(); k++) hout[qi[k]] = qv[k];
-    } else {
+    u64 launches = ctx->stats.kernel_launches;
+    if (!mx.empty()) {
+        std::vector<u64> mv(mx.size());
+        PC_TRY(multi_batch(ctx, mx, mv));
+        for (size_t k = 0; k < mx.size(); k++) hout[mi[k]] = mv[k];
+        launches = ctx->stats.kernel_launches;
+    }
+    for (size_t k = 0; k < bx.size(); k++) {
+        u64 v = 0;
         memset(&ctx->stats, 0, sizeof(ctx->stats));
+        PC_TRY(pi_count_impl(ctx, bx[k], 0, &v));
+        hout[bi[k]] = v;
+        launches += ctx->stats.kernel_launches;
     }
-    if (!sx.empty()) ctx->stats.kernel_launches++;
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.kernel_launches = launches;
     if (stream) {
         PC_CUDA(ctx, cudaMemcpyAsync(out, hout.data(), n * sizeof(u64), cudaMemcpyHostToDevice, (cudaStream_t)stream));
         PC_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));

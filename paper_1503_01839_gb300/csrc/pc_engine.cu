@@ -79,7 +79,8 @@ extern "C" void pc_destroy(pc_ctx* ctx)
     workers_destroy(ctx);
     DevBuf* bufs[] = {&ctx->seg_b, &ctx->seg_off, &ctx->counts, &ctx->tallies,
                       &ctx->acc_seg, &ctx->partials, &ctx->result, &ctx->misc, &ctx->scan_tmp, &ctx->queue,
-                      &ctx->easy_rng, &ctx->easy_chunk_off, &ctx->easy_cmap, &ctx->starts};
+                      &ctx->easy_rng, &ctx->easy_chunk_off, &ctx->easy_cmap, &ctx->starts,
+                      &ctx->mq_q, &ctx->mq_pref, &ctx->mq_e, &ctx->mq_h, &ctx->mq_hq, &ctx->mq_p};
     for (DevBuf* b : bufs) buf_free(*b);
     if (!ctx->borrowed) {
         Tables& T = ctx->T;
@@ -196,11 +197,11 @@ u32 default_alpha(u64 x)
     if (d <= 8) return 2;
     if (d == 9) return 4;
     if (d <= 11) return 6;
-    if (d <= 13) return 24;
-    if (d <= 15) return 28;
-    if (d == 16) return 32;
-    if (d == 17) return 40;
-    return 48;
+    if (d <= 13) return 16;
+    if (d == 14) return 24;
+    if (d == 15) return 20;
+    if (d <= 17) return 32;
+    return 40;
 }
 
 int decimal_digits(u64 x)

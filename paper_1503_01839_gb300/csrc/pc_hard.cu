@@ -142,16 +142,28 @@ __device__ __forceinline__ bool leaf_window(const HardArgs& A, u64 p, u64 vp, u6
 // shared-memory atomics, since lanes of one pass may share a block.
 // Instantiated for several (threads, resident CTAs) launch bounds: fewer
 // registers per thread buy more resident warps to hide shared-memory latency.
-template <int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
+// A launch over the segments of many queries (the batched form): item g is segment
+// g - qpref[q] of query q, qpref[q] <= g < qpref[q + 1], with arguments qargs[q] and its
+// local sums added to qacc[q].  Queries keep their segments whole (no replicas).
+struct MultiArgs {
+    const HardArgs* qargs;
+    const u32* qpref;   // nq + 1 entries
+    u32 nq;
+    unsigned long long items;
+    I128Pair* qacc;     // query q's sum goes to qacc[q * qstride]
+    u32 qstride;
+};
+
+template <int MAXT, int MINB, bool MULTI>
+__global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A0, MultiArgs M)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // blocks of 256 bits (four 64-bit words); each lane owns bpl consecutive blocks
-    const u32 nw = A.nw, sub_bytes = A.sub_bytes, sub_words = sub_bytes >> 2, nbw = sub_bytes >> 5, bpl = nbw >> 5;
+    const u32 nw = A0.nw, sub_bytes = A0.sub_bytes, sub_words = sub_bytes >> 2, nbw = sub_bytes >> 5, bpl = nbw >> 5;
     const u32 sub_bits = sub_bytes << 3;
     StepInfo* st = (StepInfo*)smem_raw;
     u32* bits = (u32*)(smem_raw + BATCH * sizeof(StepInfo));
-    u16* blk = (u16*)(bits + (A.seg_bytes >> 2));  // nw * nbw block counters
+    u16* blk = (u16*)(bits + (A0.seg_bytes >> 2));  // nw * nbw block counters
     u16* pre = blk + nw * nbw;                     // nw * nbw prefix counts
     u32* I = (u32*)(pre + nw * nbw);               // BATCH * (nw + 1)
     u32* cw = I + BATCH * (nw + 1);                // BATCH * nw
@@ -173,14 +185,14 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
     __shared__ RankTable lst_rank[1 + Tables::NSUB];
 
     const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5, NT = blockDim.x;
-    make_pattern_words(patw, A.k0);
+    make_pattern_words(patw, A0.k0);
     if (tid <= Tables::NSUB) {
-        const MList& l = tid == 0 ? A.ml : A.sl[tid - 1];
+        const MList& l = tid == 0 ? A0.ml : A0.sl[tid - 1];
         lst_info[tid] = l.info;
         lst_m[tid] = l.m;
         lst_gpf[tid] = l.gpf;
         lst_rcp[tid] = l.rcp;
-        lst_rank[tid] = tid == 0 ? A.rk : A.srk[tid - 1];
+        lst_rank[tid] = tid == 0 ? A0.rk : A0.srk[tid - 1];
     }
     u32* my = bits + w * sub_words;
     const u64* my64 = (const u64*)my;
@@ -207,16 +219,52 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
     i64 acc = 0;
     unsigned long long nleaves = 0, nclears = 0, nbusy = 0, nleafy = 0;
 
+    __shared__ __align__(16) unsigned char sA_raw[MULTI ? sizeof(HardArgs) : 16];
+    __shared__ u32 s_q;
+    u32 cur_q = ~0u;
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_item = atomicAdd(A.queue, 1u);
+        if (tid == 0) s_item = atomicAdd(A0.queue, 1u);
         __syncthreads();
         const u64 item = s_item;
-        if (item >= *A.nitems) break;
-        const HardItem it = A.items[item];
-        const u64 s = it.s;
+        u64 s;
+        u32 it_lo, it_hi;
+        if (MULTI) {
+            if (item >= M.items) break;
+            if (tid == 0) {   // the item's query: the last q with qpref[q] <= item
+                u32 lo = 0, hi = M.nq;
+                while (hi - lo > 1) {
+                    const u32 mid = (lo + hi) >> 1;
+                    if (M.qpref[mid] <= item) lo = mid; else hi = mid;
+                }
+                s_q = lo;
+            }
+            __syncthreads();
+            const u32 q = s_q;
+            if (q != cur_q) {   // the previous query's sums, then this query's arguments
+                if (cur_q != ~0u) {
+                    const i128 tq = block_sum_i128((i128)acc, red);
+                    if (tid == 0) mq_atomic_add_i128(M.qacc + (u64)cur_q * M.qstride, tq);
+                    acc = 0;
+                }
+                const u32* src = (const u32*)(M.qargs + q);
+                for (u32 k = tid; k < sizeof(HardArgs) / 4; k += NT) ((u32*)sA_raw)[k] = src[k];
+                cur_q = q;
+                __syncthreads();
+            }
+            s = item - M.qpref[q];
+            it_lo = ((const HardArgs*)sA_raw)->k0 + 1;
+            it_hi = ~0u;
+        } else {
+            if (item >= *A0.nitems) break;
+            const HardItem it = A0.items[item];
+            s = it.s;
+            it_lo = it.b_lo;
+            it_hi = it.b_hi;
+        }
+        const HardArgs& A = MULTI ? *(const HardArgs*)sA_raw : A0;
         const u32 Bs = A.segB[s];
-        const u32 b_first = it.b_lo, b_last = it.b_hi - 1 < Bs ? it.b_hi - 1 : Bs;   // this item's steps
+        const u32 b_first = it_lo, b_last = it_hi - 1 < Bs ? it_hi - 1 : Bs;   // this item's steps
         const u64 L = s * A.span;
         const u64 Lw = L + w * A.dspan;
 
@@ -589,6 +637,32 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
                             const u32 ps = st[t].pself;
                             if (j == 0 && ps != ~0u && (ps >> A.sub_shift) == w) pp = ps & (sub_bits - 1);   // p itself
                         }
+                        if (st[t0 + c].p >= sub_bytes) {
+                            // every prime of the pass has at most one multiple per class in the
+                            // sub-range: hits found in one go, offsets from two ballots
+                            u32 h = 0, pa = 0, pb = 0;
+                            if (by < (i32)sub_bytes) {
+                                const u32 pos = ((u32)by << 3) + bj;
+                                nclears++;
+                                if ((my[pos >> 5] >> (pos & 31)) & 1u) {
+                                    pa = pos;
+                                    h = 1;
+                                }
+                            }
+                            if (pp != ~0u && ((my[pp >> 5] >> (pp & 31)) & 1u)) {
+                                if (h) pb = pp; else pa = pp;
+                                h++;
+                            }
+                            const u32 m1 = __ballot_sync(0xffffffffu, h >= 1), m2 = __ballot_sync(0xffffffffu, h >= 2);
+                            const u32 below = (1u << lane) - 1u;
+                            const u32 off = nent + __popc(m1 & below) + __popc(m2 & below);
+                            if (h >= 1) lg[off] = (u16)pa;
+                            if (h >= 2) lg[off + 1] = (u16)pb;
+                            const u32 first = __shfl_sync(0xffffffffu, off, ((lane - c) & 3) * 8);
+                            if (lane >= c && lane < c + 4) hoff = first;
+                            nent += __popc(m1) + __popc(m2);
+                            continue;
+                        }
                         u32 h = 0;
                         for (i32 q = by; q < (i32)sub_bytes; q += p) {
                             const u32 pos = ((u32)q << 3) + bj;
@@ -860,15 +934,19 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A)
         }
     }
     i128 tot = block_sum_i128((i128)acc, red);
-    if (tid == 0) store_i128(A.acc + blockIdx.x, tot);
+    if (MULTI) {
+        if (tid == 0 && cur_q != ~0u) mq_atomic_add_i128(M.qacc + (u64)cur_q * M.qstride, tot);
+    } else {
+        if (tid == 0) store_i128(A0.acc + blockIdx.x, tot);
+    }
     for (int o = 16; o; o >>= 1) {
         nleaves += __shfl_xor_sync(0xffffffffu, nleaves, o);
         nclears += __shfl_xor_sync(0xffffffffu, nclears, o);
     }
-    if (lane == 0 && nleaves) atomicAdd(A.stat, nleaves);
-    if (lane == 0 && nclears) atomicAdd(A.stat + 1, nclears);
-    if (lane == 0 && nbusy) atomicAdd(A.stat + 2, nbusy);     // busy (warp, step) pairs
-    if (lane == 0 && nleafy) atomicAdd(A.stat + 3, nleafy);   // of which with leaves
+    if (lane == 0 && nleaves) atomicAdd(A0.stat, nleaves);
+    if (lane == 0 && nclears) atomicAdd(A0.stat + 1, nclears);
+    if (lane == 0 && nbusy) atomicAdd(A0.stat + 2, nbusy);     // busy (warp, step) pairs
+    if (lane == 0 && nleafy) atomicAdd(A0.stat + 3, nleafy);   // of which with leaves
 }
 
 // ---------------------------------------------------------- schedule
@@ -1210,6 +1288,74 @@ __global__ void __launch_bounds__(256) plan_bsplit_kernel(HardArgs A, PlanArgs P
     }
 }
 
+static size_t hard_smem(const HardArgs& A)
+{
+    static_assert(sizeof(StepInfo) % 16 == 0, "StepInfo must keep 16-byte alignment");
+    return BATCH * sizeof(StepInfo) + A.seg_bytes + (size_t)A.nw * (A.sub_bytes >> 5) * 4 +
+           (size_t)BATCH * (A.nw + 1) * 4 + 3 * (size_t)BATCH * A.nw * 4 + (size_t)BATCH * A.nw +
+           (size_t)A.nw * LOG_CAP * sizeof(u16);
+}
+
+// The instantiation: the most resident warps (registers and shared memory permitting), or
+// at least ctas_per_sm resident CTAs when that is set; *per_sm its resident CTAs (<= 8).
+template <bool MULTI>
+static int choose_hard_kernel(pc_ctx* ctx, const HardArgs& A, size_t smem, void (**out)(HardArgs, MultiArgs),
+                              int* out_per_sm)
+{
+    struct Variant {
+        void (*fn)(HardArgs, MultiArgs);
+        int maxt, minb;
+    };
+    static const Variant variants[] = {{hard_sieve_kernel<512, 1, MULTI>, 512, 1},
+                                       {hard_sieve_kernel<256, 3, MULTI>, 256, 3},
+                                       {hard_sieve_kernel<512, 2, MULTI>, 512, 2},
+                                       {hard_sieve_kernel<256, 4, MULTI>, 256, 4}};
+    const int nt = 32 * (int)A.nw;
+    const int want = (int)ctx->params.ctas_per_sm;
+    void (*kern)(HardArgs, MultiArgs) = nullptr;
+    int per_sm = 0;
+    for (const Variant& v : variants) {
+        if (nt > v.maxt) continue;
+        // The limit is a property of the kernel, shared by every host thread of the
+        // process: always raise it to the device maximum (never to this call's size),
+        // so that a concurrent query with larger segments is not cut short.
+        cudaFuncAttributes fa;
+        PC_CUDA(ctx, cudaFuncGetAttributes(&fa, v.fn));
+        const size_t dyn_max = ctx->smem_optin - fa.sharedSizeBytes;
+        if (smem > dyn_max) {
+            pc_set_error(ctx, "hard-leaf sieve: %zu bytes of shared memory per CTA", smem);
+            return PC_EINVAL;
+        }
+        cudaError_t ea = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+        if (ea != cudaSuccess) {
+            pc_set_error(ctx, "cudaFuncSetAttribute(smem=%zu): %s", dyn_max, cudaGetErrorString(ea));
+            return PC_ECUDA;
+        }
+        int fit = 0;   // resident CTAs the SM can hold (registers and shared memory)
+        PC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, v.fn, nt, smem));
+        if (fit < 1) continue;
+        if (want) {
+            // the least register-constrained variant reaching the requested residency
+            if (!kern || (per_sm < want && fit > per_sm)) {
+                kern = v.fn;
+                per_sm = fit;
+            }
+        } else if (fit > per_sm) {
+            kern = v.fn;
+            per_sm = fit;
+        }
+    }
+    if (!kern) {
+        pc_set_error(ctx, "hard-leaf sieve: no launch configuration fits (smem=%zu, threads=%d)", smem, nt);
+        return PC_EINVAL;
+    }
+    if (want && per_sm > want) per_sm = want;
+    if (per_sm > 8) per_sm = 8;   // 32 KiB segments fit 4; smaller ones (autotuned, or set) up to 8
+    *out = kern;
+    *out_per_sm = per_sm;
+    return PC_OK;
+}
+
 int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 {
     HardArgs A{};
@@ -1296,61 +1442,10 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
         return PC_EOVERFLOW;
     }
 
-    const u32 nbw = A.sub_bytes >> 7;
-    (void)nbw;
-    static_assert(sizeof(StepInfo) % 16 == 0, "StepInfo must keep 16-byte alignment");
-    const size_t smem = BATCH * sizeof(StepInfo) + A.seg_bytes + (size_t)A.nw * (A.sub_bytes >> 5) * 4 +
-                        (size_t)BATCH * (A.nw + 1) * 4 + 3 * (size_t)BATCH * A.nw * 4 +
-                        (size_t)BATCH * A.nw + (size_t)A.nw * LOG_CAP * sizeof(u16);
-    // the instantiation: the most resident warps (registers and shared memory
-    // permitting), or at least ctas_per_sm resident CTAs when that is set
-    struct Variant {
-        void (*fn)(HardArgs);
-        int maxt, minb;
-    };
-    static const Variant variants[] = {{hard_sieve_kernel<512, 1>, 512, 1}, {hard_sieve_kernel<256, 3>, 256, 3},
-                                       {hard_sieve_kernel<512, 2>, 512, 2}, {hard_sieve_kernel<256, 4>, 256, 4}};
-    const int nt = 32 * (int)A.nw;
-    const int want = (int)ctx->params.ctas_per_sm;
-    void (*kern)(HardArgs) = nullptr;
+    const size_t smem = hard_smem(A);
+    void (*kern)(HardArgs, MultiArgs) = nullptr;
     int per_sm = 0;
-    for (const Variant& v : variants) {
-        if (nt > v.maxt) continue;
-        // The limit is a property of the kernel, shared by every host thread of the
-        // process: always raise it to the device maximum (never to this call's size),
-        // so that a concurrent query with larger segments is not cut short.
-        cudaFuncAttributes fa;
-        PC_CUDA(ctx, cudaFuncGetAttributes(&fa, v.fn));
-        const size_t dyn_max = ctx->smem_optin - fa.sharedSizeBytes;
-        if (smem > dyn_max) {
-            pc_set_error(ctx, "hard-leaf sieve: %zu bytes of shared memory per CTA", smem);
-            return PC_EINVAL;
-        }
-        cudaError_t ea = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
-        if (ea != cudaSuccess) {
-            pc_set_error(ctx, "cudaFuncSetAttribute(smem=%zu): %s", dyn_max, cudaGetErrorString(ea));
-            return PC_ECUDA;
-        }
-        int fit = 0;   // resident CTAs the SM can hold (registers and shared memory)
-        PC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, v.fn, nt, smem));
-        if (fit < 1) continue;
-        if (want) {
-            // the least register-constrained variant reaching the requested residency
-            if (!kern || (per_sm < want && fit > per_sm)) {
-                kern = v.fn;
-                per_sm = fit;
-            }
-        } else if (fit > per_sm) {
-            kern = v.fn;
-            per_sm = fit;
-        }
-    }
-    if (!kern) {
-        pc_set_error(ctx, "hard-leaf sieve: no launch configuration fits (smem=%zu, threads=%d)", smem, nt);
-        return PC_EINVAL;
-    }
-    if (want && per_sm > want) per_sm = want;
-    if (per_sm > 8) per_sm = 8;   // 32 KiB segments fit 4; smaller ones (autotuned, or set) up to 8
+    PC_TRY(choose_hard_kernel<false>(ctx, A, smem, &kern, &per_sm));
     int ctas = ctx->sm_count * per_sm;
 
     // per-segment leaf estimate, then the work items, all on the device
@@ -1393,7 +1488,7 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 
     cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
     PC_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-    kern<<<ctas, nt, smem, ctx->stream>>>(A);
+    kern<<<ctas, 32 * A.nw, smem, ctx->stream>>>(A, MultiArgs{});
     PC_LAUNCHED(ctx);
     PC_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
     ctx->stats.kernel_launches++;
@@ -1425,5 +1520,201 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     ctx->stats.segments = A.nseg;
     ctx->stats.steps = total;
     ctx->stats.seg_bytes = A.seg_bytes;
+    return PC_OK;
+}
+
+// ------------------------------------------------------- many queries at once
+// The hard leaves of every pi(x) query of a batch in one sieve launch over all their
+// segments (largest queries first, since the batch sorts them so), with the segment
+// schedule and the count rows of every query built by one launch each.
+
+// B_s and the reciprocals of L_s, L_s + span for segment g - pref[q] of query q
+__global__ void mq_seg_b_kernel(const HardArgs* qa, const u64* pref, u32 Q, u32* segB, u64* rcp_seg)
+{
+    const u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= pref[Q]) return;
+    const u64 q = mq_find(pref, Q + 1, g);
+    const HardArgs& A = qa[q];
+    const u64 s = g - pref[q];
+    rcp_seg[2 * g] = s ? ~0ull / (s * A.span) : 0;
+    rcp_seg[2 * g + 1] = ~0ull / ((s + 1) * A.span);
+    u32 B = A.bmax;
+    if (s > 0) {
+        const u64 r = pc_isqrt(A.x / (s * A.span));
+        const u64 pr = pi_lookup(A.pit, r);
+        if (pr < B) B = (u32)pr;
+    }
+    segB[g] = B;
+}
+
+// row b = k0 + g - rpref[q] of query q: the number of its segments with B_s >= b
+__global__ void mq_row_len_kernel(const HardArgs* qa, const u64* rpref, u32 Q, u32* len)
+{
+    const u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= rpref[Q]) return;
+    const u64 q = mq_find(rpref, Q + 1, g);
+    const HardArgs& A = qa[q];
+    const u32 b = A.k0 + (u32)(g - rpref[q]);
+    u64 lo = 0, hi = A.nseg;   // first s with segB[s] < b
+    while (lo < hi) {
+        const u64 mid = (lo + hi) >> 1;
+        if (A.segB[mid] >= b) lo = mid + 1; else hi = mid;
+    }
+    len[g] = (u32)lo;
+}
+
+// the carries: a warp per (query, b), kleaf < b <= bmax: the exclusive scan over
+// segments of count(., b - 1) dotted with tally(., b), into the query's hard part
+__global__ void mq_combine_kernel(const HardArgs* qa, const u64* cpref, u32 Q, I128Pair* parts)
+{
+    const u32 lane = threadIdx.x & 31;
+    const u64 gw = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 g = gw; g < cpref[Q]; g += nwarps) {
+        const u64 q = mq_find(cpref, Q + 1, g);
+        const HardArgs& A = qa[q];
+        const u32 b = A.kleaf + 1 + (u32)(g - cpref[q]);
+        const u64 row = A.off[b - A.k0], Sb = A.off[b - A.k0 + 1] - row, prow = A.off[b - 1 - A.k0];
+        u64 carry = 0;
+        i128 dot = 0;
+        for (u64 base = 0; base < Sb; base += 32) {
+            const u64 s = base + lane;
+            const u64 v = s < Sb ? (u64)A.counts[prow + s] : 0;
+            u64 incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const u64 t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (s < Sb) {
+                const i32 tl = A.tallies[row + s];
+                if (tl) dot += (i128)tl * (i128)(carry + incl - v);
+            }
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        dot = warp_sum_i128(dot);
+        if (lane == 0 && dot != 0) mq_atomic_add_i128(parts + 5 * q + 3, dot);
+    }
+}
+
+int mq_hard(pc_ctx* ctx, const MQPlan& P)
+{
+    const u32 Q = P.Q;
+    HardArgs T{};   // what every query of the batch shares: tables, geometry, queue, counters
+    T.k0 = 5;
+    T.kleaf = 5;
+    T.seg_bytes = pc_seg_bytes(ctx, 16384);
+    T.sub_bytes = pc_sub_bytes(ctx, T.seg_bytes);
+    T.nw = T.seg_bytes / T.sub_bytes;
+    T.sub_shift = 3;
+    while ((1u << T.sub_shift) < T.sub_bytes * 8) T.sub_shift++;
+    T.span = 30ull * T.seg_bytes;
+    T.dspan = 30ull * T.sub_bytes;
+    T.pit = ctx->T.pi();
+    T.rk = ctx->T.rank();
+    T.ml = ctx->T.mlist();
+    T.nsl = ctx->T.n_sl;
+    for (int k = 0; k < Tables::NSUB; k++) {
+        T.sl[k] = ctx->T.sublist(k);
+        T.srk[k] = ctx->T.subrank(k);
+        T.slK[k] = k < (int)T.nsl ? ctx->T.sl_K[k] : ~0u;
+    }
+    T.primes = ctx->T.primes.as<u32>();
+    T.primes_rcp = ctx->T.primes_rcp.as<u64>();
+    // per query: segments, count rows b = k0 .. bmax, carried rows b = kleaf + 1 .. bmax
+    std::vector<u64> spref(Q + 1, 0), rpref(Q + 1, 0), cpref(Q + 1, 0);
+    std::vector<u32> ipref(Q + 1, 0);
+    u64 bound = 0;   // count-row entries: at most segments x rows per query
+    for (u32 q = 0; q < Q; q++) {
+        const MQ& m = P.hq[q];
+        const u64 bmax = m.B < m.a ? m.B : m.a;
+        const bool work = m.c == 5 && bmax > T.kleaf;
+        const u64 nseg = work ? m.z / T.span + 1 : 0;
+        const u64 nrows = work ? bmax - T.k0 + 1 : 0;
+        spref[q + 1] = spref[q] + nseg;
+        rpref[q + 1] = rpref[q] + nrows;
+        cpref[q + 1] = cpref[q] + (work ? bmax - T.kleaf : 0);
+        bound += nseg * nrows;
+    }
+    const u64 S = spref[Q], R = rpref[Q];
+    if (S == 0) return PC_OK;
+    if (bound >> 32 || S >> 32) {
+        pc_set_error(ctx, "batch: %llu count-row entries exceed 32-bit offsets", (unsigned long long)bound);
+        return PC_EOVERFLOW;
+    }
+    for (u32 q = 0; q <= Q; q++) ipref[q] = (u32)spref[q];
+    // mq_h: spref | rpref | cpref (Q+1 u64 each) | ipref (Q+1 u32) | segB (S u32) | rcp_seg (2S u64) |
+    // rowlen (R u32) | off (R+1 u64) | queue + counters (128 B)
+    auto al = [](size_t v) { return (v + 15) / 16 * 16; };
+    const size_t o_r = al((Q + 1) * 8), o_c = o_r + al((Q + 1) * 8), o_i = o_c + al((Q + 1) * 8);
+    const size_t o_sb = o_i + al((Q + 1) * 4), o_rc = o_sb + al(S * 4), o_rl = o_rc + al(2 * S * 8);
+    const size_t o_off = o_rl + al(R * 4), o_q = o_off + al((R + 1) * 8), total = o_q + 128;
+    PC_TRY(buf_reserve(ctx, ctx->mq_h, total));
+    PC_TRY(buf_reserve(ctx, ctx->mq_hq, Q * sizeof(HardArgs)));
+    PC_TRY(buf_reserve(ctx, ctx->counts, bound * sizeof(u32)));
+    PC_TRY(buf_reserve(ctx, ctx->tallies, bound * sizeof(i32)));
+    unsigned char* base = ctx->mq_h.as<unsigned char>();
+    u64* d_spref = (u64*)base;
+    u64* d_rpref = (u64*)(base + o_r);
+    u64* d_cpref = (u64*)(base + o_c);
+    u32* d_ipref = (u32*)(base + o_i);
+    u32* d_segB = (u32*)(base + o_sb);
+    u64* d_rcp = (u64*)(base + o_rc);
+    u32* d_rowlen = (u32*)(base + o_rl);
+    u64* d_off = (u64*)(base + o_off);
+    u32* d_queue = (u32*)(base + o_q);
+    HardArgs* d_qa = ctx->mq_hq.as<HardArgs>();
+    std::vector<HardArgs> qa(Q, T);
+    for (u32 q = 0; q < Q; q++) {
+        const MQ& m = P.hq[q];
+        HardArgs& A = qa[q];
+        A.x = m.x;
+        A.y = m.y;
+        A.z = m.z;
+        A.c = m.c;
+        A.a = m.a;
+        A.trunc = false;
+        const u64 bmax = m.B < m.a ? m.B : m.a;
+        A.bmax = (u32)pc_max(bmax, T.k0);
+        A.nseg = spref[q + 1] - spref[q];
+        A.s0 = 0;
+        A.s1 = A.nseg;
+        A.rcp_y = ~0ull / m.y;
+        A.segB = d_segB + spref[q];
+        A.rcp_seg = d_rcp + 2 * spref[q];
+        A.off = d_off + rpref[q];
+        A.start = nullptr;
+        A.counts = ctx->counts.as<u32>();
+        A.tallies = ctx->tallies.as<i32>();
+        A.queue = d_queue;
+        A.stat = (unsigned long long*)(d_queue + 2);
+    }
+    cudaStream_t st = ctx->stream;
+    PC_CUDA(ctx, cudaMemcpyAsync(d_qa, qa.data(), Q * sizeof(HardArgs), cudaMemcpyHostToDevice, st));
+    PC_CUDA(ctx, cudaMemcpyAsync(d_spref, spref.data(), (Q + 1) * 8, cudaMemcpyHostToDevice, st));
+    PC_CUDA(ctx, cudaMemcpyAsync(d_rpref, rpref.data(), (Q + 1) * 8, cudaMemcpyHostToDevice, st));
+    PC_CUDA(ctx, cudaMemcpyAsync(d_cpref, cpref.data(), (Q + 1) * 8, cudaMemcpyHostToDevice, st));
+    PC_CUDA(ctx, cudaMemcpyAsync(d_ipref, ipref.data(), (Q + 1) * 4, cudaMemcpyHostToDevice, st));
+    PC_CUDA(ctx, cudaMemsetAsync(d_queue, 0, 128, st));
+    PC_CUDA(ctx, cudaMemsetAsync(ctx->tallies.p, 0, bound * sizeof(i32), st));
+    mq_seg_b_kernel<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(d_qa, d_spref, Q, d_segB, d_rcp);
+    PC_LAUNCHED(ctx);
+    mq_row_len_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(d_qa, d_rpref, Q, d_rowlen);
+    PC_LAUNCHED(ctx);
+    PC_TRY(scan_exclusive_u32_to_u64(ctx, d_rowlen, d_off, R));
+    // the sieve: items are the segments of every query, handed out in order
+    T.queue = d_queue;
+    T.stat = (unsigned long long*)(d_queue + 2);
+    const size_t smem = hard_smem(T);
+    void (*kern)(HardArgs, MultiArgs) = nullptr;
+    int per_sm = 0;
+    PC_TRY(choose_hard_kernel<true>(ctx, T, smem, &kern, &per_sm));
+    const u64 ctas = pc_min((u64)ctx->sm_count * per_sm, S);
+    MultiArgs M{d_qa, d_ipref, Q, (unsigned long long)S, P.parts + 3, 5u};
+    kern<<<(unsigned)ctas, 32 * T.nw, smem, st>>>(T, M);
+    PC_LAUNCHED(ctx);
+    if (cpref[Q]) {
+        mq_combine_kernel<<<ctx->sm_count * 8, 256, 0, st>>>(d_qa, d_cpref, Q, P.parts);
+        PC_LAUNCHED(ctx);
+    }
+    ctx->stats.kernel_launches += 4;
     return PC_OK;
 }

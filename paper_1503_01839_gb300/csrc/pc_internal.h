@@ -104,6 +104,7 @@ struct pc_ctx {
     // scratch (grow-only)
     DevBuf seg_b, seg_off, counts, tallies, acc_seg, partials, result, misc, scan_tmp, queue;
     DevBuf easy_rng, easy_chunk_off, easy_cmap, starts;
+    DevBuf mq_q, mq_pref, mq_e, mq_h, mq_hq, mq_p;   // batched queries (pc_pi_count_batch)
     // pinned host staging for small results
     void* host_stage = nullptr;
     pc_stats stats{};
@@ -183,6 +184,55 @@ int run_easy(pc_ctx* ctx, const LeafProblem& P, I128Pair* out);
 int run_hard_smallb(pc_ctx* ctx, const LeafProblem& P, I128Pair* out);
 int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out);
 int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out);
+
+// ------------------------------------------------------- batched queries
+// One pi(x) query of a batched launch (pc_pi_count_batch): its parameters, and the
+// table values the batch reads back once for all queries.
+struct MQ {
+    u64 x, y, z;
+    u64 a;      // pi(y)
+    u64 B;      // pi(isqrt z)
+    u64 K;      // pi(isqrt x)
+    u64 nlim;   // m-list entries with m <= y
+    u64 E;      // pi(iroot3 x): the easy leaves have b <= E
+    u32 c;
+    u32 pad;
+};
+
+// The parts of every query of a batch, [q][0..4] = S1, trivial, easy, hard, P2, summed
+// exactly by atomic_add_i128 (any order).
+struct MQPlan {
+    u32 Q = 0;
+    const MQ* dq = nullptr;      // device copy of hq
+    I128Pair* parts = nullptr;   // device, Q x 5
+    std::vector<MQ> hq;
+};
+
+__device__ __forceinline__ void mq_atomic_add_i128(I128Pair* p, i128 v)
+{
+    // the low words add with wrap-around; every addition sends its own carry to the high word
+    const unsigned long long lo = (unsigned long long)(u64)v;
+    const unsigned long long old = atomicAdd((unsigned long long*)&p->lo, lo);
+    const u64 carry = old + lo < old ? 1u : 0u;
+    atomicAdd((unsigned long long*)&p->hi, (unsigned long long)((u64)(i64)(v >> 64) + carry));
+}
+
+// the last index k < n with pref[k] <= v (pref ascending, pref[0] <= v)
+__device__ __forceinline__ u64 mq_find(const u64* pref, u64 n, u64 v)
+{
+    u64 lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const u64 mid = (lo + hi) >> 1;
+        if (pref[mid] <= v) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+int mq_info(pc_ctx* ctx, MQPlan& P);          // fills a, B, K, nlim, E (one read-back for the batch)
+int mq_s1_trivial(pc_ctx* ctx, const MQPlan& P);
+int mq_easy(pc_ctx* ctx, const MQPlan& P);
+int mq_hard(pc_ctx* ctx, const MQPlan& P);
+int mq_p2(pc_ctx* ctx, const MQPlan& P);
 
 // segment geometry shared by the sieve kernels
 struct SegGeom {

@@ -47,6 +47,10 @@ __device__ __forceinline__ u64 pi_sampled(const LeafArgs& A, u64 v, u64* pv)
     return k;
 }
 
+// a lane walks clust_chunk / 32 primes of a clustered chunk: long slices keep
+// more of a run in one lane, short ones balance the warps when there are few
+PC_HD u32 clust_chunk_for(u64 x) { return x >= 100000000000000000ull ? 16384 : 8192; }
+
 static LeafArgs make_args(pc_ctx* ctx, const LeafProblem& P, u64 n_lim)
 {
     LeafArgs A;
@@ -64,9 +68,7 @@ static LeafArgs make_args(pc_ctx* ctx, const LeafProblem& P, u64 n_lim)
     A.samp = ctx->T.samp.as<u32>();
     A.samp_s = ctx->T.samp_s;
     A.sampled = ctx->params.pi_gather == 1;
-    // a lane walks clust_chunk / 32 primes of a clustered chunk: long slices keep
-    // more of a run in one lane, short ones balance the warps when there are few
-    A.clust_chunk = P.x >= 100000000000000000ull ? 16384 : 8192;
+    A.clust_chunk = clust_chunk_for(P.x);
     return A;
 }
 
@@ -193,22 +195,21 @@ __host__ __device__ inline u64 easy_chunks(const EasyRange& r, u32 clust_chunk)
     return (r.im - r.i0 + EASY_CHUNK - 1) / EASY_CHUNK + (r.i1 - r.im + clust_chunk - 1) / clust_chunk;
 }
 
-__global__ void easy_ranges_kernel(LeafArgs A, u64 b_lo, u64 nb, EasyRange* rng, u32* nchunk)
+// The easy leaves of prime p_b for a query (x, y, a): list indices [i0, i1) of the
+// m-list, or of the primes when p_b^2 > y, and where the clustered part starts.
+__device__ __forceinline__ EasyRange easy_range(const LeafArgs& A, u64 x, u64 y, u64 a, u64 b)
 {
-    u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nb) return;
-    u64 b = b_lo + t;
-    u64 p = A.primes[b];
-    u64 xp = A.x / p;
-    u64 T = pc_min(p * p, A.y);
-    u64 lo = pc_max(A.y / p, xp / T);
-    u64 hi = pc_min(A.y, xp / p);
+    const u64 p = A.primes[b];
+    const u64 xp = x / p;
+    const u64 T = pc_min(p * p, y);
+    const u64 lo = pc_max(y / p, xp / T);
+    const u64 hi = pc_min(y, xp / p);
     EasyRange r{0, 0, 0, 0, 0};
     if (hi > lo) {
-        if (p * p > A.y) {
+        if (p * p > y) {
             // lpf(m) > p_b and m <= y < p_b^2: m is a prime q, p_b < q <= p_a
             u64 k0 = pc_max(pi_lookup(A.pit, lo), b);
-            u64 k1 = pc_min(pi_lookup(A.pit, hi), A.a);
+            u64 k1 = pc_min(pi_lookup(A.pit, hi), a);
             if (k1 > k0) {
                 r.i0 = k0 + 1;
                 r.i1 = k1 + 1;
@@ -224,6 +225,14 @@ __global__ void easy_ranges_kernel(LeafArgs A, u64 b_lo, u64 nb, EasyRange* rng,
         }
     }
     if (r.src == 0) r.im = r.i1;
+    return r;
+}
+
+__global__ void easy_ranges_kernel(LeafArgs A, u64 b_lo, u64 nb, EasyRange* rng, u32* nchunk)
+{
+    u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    const EasyRange r = easy_range(A, A.x, A.y, A.a, b_lo + t);
     rng[t] = r;
     nchunk[t] = (u32)easy_chunks(r, A.clust_chunk);
 }
@@ -234,6 +243,111 @@ __global__ void easy_chunk_map_kernel(u64 nb, const u64* choff, u32* cmap)
     const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nb) return;
     for (u64 ch = choff[t]; ch < choff[t + 1]; ch++) cmap[ch] = (u32)t;
+}
+
+// One chunk of the easy leaves of p_b (query x, a): chunk c of range r, walked by the
+// 32 lanes of a warp; adds this lane's share of the sum to s.
+template <bool SAMPLED>
+__device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 b, const EasyRange& r, u64 c, u32 cc,
+                                           u32 lane, i64& s, u32& n_one, u32& n_runs, u32& n_run_leaves)
+{
+    const u64 nsp = (r.im - r.i0 + EASY_CHUNK - 1) / EASY_CHUNK;
+    const u64 p = A.primes[b];
+    const u64 xp = div_rcp(x, p, A.primes_rcp[b]);
+    if (c >= nsp) {
+        // clustered chunk: each thread walks the runs of its slice of primes q
+        const u64 per = cc / 32;
+        const u64 start = r.im + (c - nsp) * cc + lane * per;
+        const u64 end = pc_min(r.i1, start + per);
+        if (start < end) {
+            const u64 qlast = A.primes[end - 1];
+            const float xpf = (float)xp;
+            for (u64 i = start; i < end;) {
+                const u64 u = div_rcp(xp, A.primes[i], A.primes_rcp[i]);
+                u64 l, pl = 0, w = 0, bits = 0;
+                u32 hb0 = 0;
+                if (SAMPLED) {
+                    l = pi_sampled(A, u, &pl);
+                } else {
+                    // pi(u) from u's record (u >= p_b >= 13, so 2, 3 and 5 all count)
+                    // u < y < 2^32: the record is u / 240, its bit from u / 30 and u % 30
+                    const u32 u32v = (u32)u, q30 = u32v / 30;
+                    w = q30 >> 3;
+                    const u32 e = 8 * (q30 & 7) + cntle30(u32v - 30 * q30);
+                    const uint4 rq = __ldg((const uint4*)(A.pit.rec + w));
+                    // the bits of the primes <= u, at the top of the word (shifted by 64 - e)
+                    bits = low_bits_top((u64)rq.x | ((u64)rq.y << 32), e);
+                    l = 3 + rq.z + __popcll(bits);
+                    hb0 = e - 1;
+                }
+                u64 n = 1;
+                if (i + 1 < end) {
+                    if (!SAMPLED) {
+                        // p_l, the largest prime <= u, from the same record when it holds one
+                        if (bits) {
+                            const u32 hb = hb0 - __clzll((long long)bits);   // its bit in the record
+                            pl = 240 * w + 30 * (hb >> 3) + r8(hb & 7);
+                        } else {
+                            pl = A.primes[l];
+                        }
+                    }
+                    // the run: primes q' <= (x/p_b) / p_l.  The quotient is estimated in
+                    // single precision and made exact with integer remainders.
+                    const float rc = __frcp_rn((float)pl);
+                    i64 qb = (i64)(xpf * rc);
+                    i64 rem = (i64)xp - qb * (i64)pl;
+                    const i64 d = (i64)floorf((float)rem * rc);
+                    qb += d;
+                    rem -= d * (i64)pl;
+                    while (rem < 0) { qb--; rem += (i64)pl; }
+                    while (rem >= (i64)pl) { qb++; rem -= (i64)pl; }
+                    const u64 bound = (u64)qb;
+                    u64 pb;
+                    n = bound >= qlast ? end - i
+                                       : (SAMPLED ? pi_sampled(A, bound, &pb) : pi_lookup(A.pit, bound)) - i + 1;
+                }
+                s += (i64)n * ((i64)l - (i64)b + 2);
+                n_runs++;
+                n_run_leaves += (u32)n;
+                i += n;
+            }
+        }
+        return;
+    }
+    const u64 start = r.i0 + c * EASY_CHUNK;
+    const u64 end = pc_min(r.im, start + EASY_CHUNK);
+    for (u64 i = start + lane; i < end; i += 32) {
+        u64 m, v;
+        bool neg = true;
+        if (r.src) {
+            m = A.primes[i];
+            v = A.primes_rcp[i];
+        } else {
+            const u32 info = A.ml.info[i];
+            if ((info >> 1) <= b) continue;
+            if (A.trunc && A.ml.gpf[i] > a) continue;
+            m = A.ml.m[i];
+            v = A.ml.rcp[i];
+            neg = info & 1;
+        }
+        // easy: p_b <= u < y < 2^32; for b > 3, u >= 7 and pi(u) counts 2, 3, 5
+        const u32 u = (u32)div_rcp(xp, m, v);
+        u64 piu;
+        if (SAMPLED) {
+            u64 pv;
+            piu = pi_sampled(A, u, &pv);
+        } else {
+            const u32 q30 = u / 30, w = q30 >> 3;
+            const u32 e = 8 * (q30 & 7) + cntle30(u - 30 * q30);   // 0..64
+            const uint4 q = __ldg((const uint4*)(A.pit.rec + w));
+            const u32 c = __popcll(low_bits_top((u64)q.x | ((u64)q.y << 32), e));
+            const u32 small = b > 3 ? 3u : (u >= 2) + (u >= 3) + (u >= 5);
+            piu = small + q.z + c;
+        }
+        const i64 t2 = (i64)piu - (i64)b + 2;
+        s += neg ? t2 : -t2;
+        n_one++;
+    }
 }
 
 // SAMPLED: read pi(u) from the sampled table instead of the popcount table
@@ -253,106 +367,9 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
         ch = __shfl_sync(0xffffffffu, ch, 0);
         if (ch >= nchunks) break;
         const u64 t = cmap[ch];
-        u64 b = b_lo + t;
-        EasyRange r = rng[t];
-        const u64 c = ch - choff[t];
-        const u64 nsp = (r.im - r.i0 + EASY_CHUNK - 1) / EASY_CHUNK;
-        u64 p = A.primes[b];
-        u64 xp = div_rcp(A.x, p, A.primes_rcp[b]);
-        if (c >= nsp) {
-            // clustered chunk: each thread walks the runs of its slice of primes q
-            const u64 per = A.clust_chunk / 32;
-            const u64 start = r.im + (c - nsp) * A.clust_chunk + lane * per;
-            const u64 end = pc_min(r.i1, start + per);
-            if (start < end) {
-                const u64 qlast = A.primes[end - 1];
-                const float xpf = (float)xp;
-                for (u64 i = start; i < end;) {
-                    const u64 u = div_rcp(xp, A.primes[i], A.primes_rcp[i]);
-                    u64 l, pl = 0, w = 0, bits = 0;
-                    u32 hb0 = 0;
-                    if (SAMPLED) {
-                        l = pi_sampled(A, u, &pl);
-                    } else {
-                        // pi(u) from u's record (u >= p_b >= 13, so 2, 3 and 5 all count)
-                        // u < y < 2^32: the record is u / 240, its bit from u / 30 and u % 30
-                        const u32 u32v = (u32)u, q30 = u32v / 30;
-                        w = q30 >> 3;
-                        const u32 e = 8 * (q30 & 7) + cntle30(u32v - 30 * q30);
-                        const uint4 rq = __ldg((const uint4*)(A.pit.rec + w));
-                        // the bits of the primes <= u, at the top of the word (shifted by 64 - e)
-                        bits = low_bits_top((u64)rq.x | ((u64)rq.y << 32), e);
-                        l = 3 + rq.z + __popcll(bits);
-                        hb0 = e - 1;
-                    }
-                    u64 n = 1;
-                    if (i + 1 < end) {
-                        if (!SAMPLED) {
-                            // p_l, the largest prime <= u, from the same record when it holds one
-                            if (bits) {
-                                const u32 hb = hb0 - __clzll((long long)bits);   // its bit in the record
-                                pl = 240 * w + 30 * (hb >> 3) + r8(hb & 7);
-                            } else {
-                                pl = A.primes[l];
-                            }
-                        }
-                        // the run: primes q' <= (x/p_b) / p_l.  The quotient is estimated in
-                        // single precision and made exact with integer remainders.
-                        const float rc = __frcp_rn((float)pl);
-                        i64 qb = (i64)(xpf * rc);
-                        i64 rem = (i64)xp - qb * (i64)pl;
-                        const i64 d = (i64)floorf((float)rem * rc);
-                        qb += d;
-                        rem -= d * (i64)pl;
-                        while (rem < 0) { qb--; rem += (i64)pl; }
-                        while (rem >= (i64)pl) { qb++; rem -= (i64)pl; }
-                        const u64 bound = (u64)qb;
-                        u64 pb;
-                        n = bound >= qlast ? end - i
-                                           : (SAMPLED ? pi_sampled(A, bound, &pb) : pi_lookup(A.pit, bound)) - i + 1;
-                    }
-                    s += (i64)n * ((i64)l - (i64)b + 2);
-                    n_runs++;
-                    n_run_leaves += (u32)n;
-                    i += n;
-                }
-            }
-            continue;
-        }
-        const u64 start = r.i0 + c * EASY_CHUNK;
-        const u64 end = pc_min(r.im, start + EASY_CHUNK);
-        for (u64 i = start + lane; i < end; i += 32) {
-            u64 m, v;
-            bool neg = true;
-            if (r.src) {
-                m = A.primes[i];
-                v = A.primes_rcp[i];
-            } else {
-                const u32 info = A.ml.info[i];
-                if ((info >> 1) <= b) continue;
-                if (A.trunc && A.ml.gpf[i] > A.a) continue;
-                m = A.ml.m[i];
-                v = A.ml.rcp[i];
-                neg = info & 1;
-            }
-            // easy: p_b <= u < y < 2^32; for b > 3, u >= 7 and pi(u) counts 2, 3, 5
-            const u32 u = (u32)div_rcp(xp, m, v);
-            u64 piu;
-            if (SAMPLED) {
-                u64 pv;
-                piu = pi_sampled(A, u, &pv);
-            } else {
-                const u32 q30 = u / 30, w = q30 >> 3;
-                const u32 e = 8 * (q30 & 7) + cntle30(u - 30 * q30);   // 0..64
-                const uint4 q = __ldg((const uint4*)(A.pit.rec + w));
-                const u32 c = __popcll(low_bits_top((u64)q.x | ((u64)q.y << 32), e));
-                const u32 small = b > 3 ? 3u : (u >= 2) + (u >= 3) + (u >= 5);
-                piu = small + q.z + c;
-            }
-            const i64 t2 = (i64)piu - (i64)b + 2;
-            s += neg ? t2 : -t2;
-            n_one++;
-        }
+        const EasyRange r = rng[t];
+        easy_chunk<SAMPLED>(A, A.x, A.a, b_lo + t, r, ch - choff[t], A.clust_chunk, lane, s, n_one, n_runs,
+                            n_run_leaves);
     }
     if (stat) {
         const u32 a0 = __reduce_add_sync(0xffffffffu, n_one), a1 = __reduce_add_sync(0xffffffffu, n_runs);
@@ -466,4 +483,173 @@ int run_hard_smallb(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
         ctx->stats.kernel_launches++;
     }
     return reduce_i128(ctx, ctx->partials.as<I128Pair>(), g, out);
+}
+
+// ----------------------------------------------------------- many queries at once
+// The leaf sums of the pi(x) queries of a batch, each phase one launch over all of
+// them: the same arithmetic as the single-query kernels above, with each query's
+// x, y, a, c read from its MQ record and its sums added to its parts.
+
+static LeafArgs table_args(pc_ctx* ctx)
+{
+    LeafProblem P{};
+    P.x = 0;
+    return make_args(ctx, P, 0);
+}
+
+// per query: pi(y), pi(isqrt z), pi(isqrt x), the m-list entries up to y, pi(iroot3 x);
+// and the ordinary leaf n = 1, phi(x, c), into S1
+__global__ void mq_info_kernel(PiTable pit, RankTable rk, MQ* qs, u32 Q, const u32* phiT, u32 Qc, I128Pair* parts)
+{
+    const u32 q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
+    MQ m = qs[q];
+    m.a = pi_lookup(pit, m.y);
+    m.B = pi_lookup(pit, pc_isqrt(m.z));
+    m.K = pi_lookup(pit, pc_isqrt(m.x));
+    m.nlim = rank_lookup(rk, m.y);
+    m.E = pi_lookup(pit, pc_iroot3(m.x));
+    qs[q] = m;
+    const u64 v = m.x / Qc;
+    const u32 r = (u32)(m.x - v * Qc);
+    store_i128(parts + 5 * q, (i128)(v * phiT[Qc] + phiT[r + 1]));   // n = 1 (c = 5 for every batched query)
+}
+
+int mq_info(pc_ctx* ctx, MQPlan& P)
+{
+    PC_TRY(tables_phi_c(ctx, 5));
+    mq_info_kernel<<<(P.Q + 127) / 128, 128, 0, ctx->stream>>>(ctx->T.pi(), ctx->T.rank(), (MQ*)P.dq, P.Q,
+                                                               ctx->T.phiT[5].as<u32>(), 2310, P.parts);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    PC_CUDA(ctx, cudaMemcpyAsync(P.hq.data(), P.dq, P.Q * sizeof(MQ), cudaMemcpyDeviceToHost, ctx->stream));
+    PC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return PC_OK;
+}
+
+// S1 (ordinary leaves n = m > 1) and the trivial leaves of every m-list entry m <= y of
+// every query; thread k takes a contiguous run of the flattened (query, entry) space
+__global__ void mq_s1_trivial_kernel(LeafArgs T, const MQ* qs, const u64* pref, u32 Q, const u32* phiT, u32 Qc,
+                                     I128Pair* parts)
+{
+    const u64 total = pref[Q];
+    const u64 nth = (u64)gridDim.x * blockDim.x, k = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 per = (total + nth - 1) / nth;
+    u64 g = k * per;
+    const u64 gend = pc_min(g + per, total);
+    if (g >= gend) return;
+    u64 q = mq_find(pref, Q + 1, g);
+    while (g < gend) {
+        const MQ m = qs[q];
+        const u64 qend = pc_min(gend, pref[q + 1]);
+        i128 s1 = 0;
+        i64 tr = 0;
+        for (; g < qend; g++) {
+            const u64 i = g - pref[q];
+            const u32 info = T.ml.info[i];
+            const u64 kb = info >> 1;
+            if (kb <= m.c) continue;
+            const u64 mv = T.ml.m[i], rc = T.ml.rcp[i];
+            const u64 xm = div_rcp(m.x, mv, rc);
+            const u64 v = xm / Qc;
+            const u64 f = v * phiT[Qc] + phiT[(u32)(xm - v * Qc) + 1];
+            s1 += (info & 1) ? -(i128)f : (i128)f;
+            if (kb > m.c + 1) {   // trivial leaves of m: max(c, pi(T)) < b < lpf index, b <= a
+                const u64 Tm = pc_max(div_rcp(m.y, mv, rc), pc_isqrt(xm));
+                const u64 hi = pc_min(kb - 1, m.a);
+                u64 lo = m.c;
+                if (Tm >= 2) lo = pc_max(lo, pi_lookup(T.pit, Tm));
+                if (hi > lo) tr += (info & 1) ? (i64)(hi - lo) : -(i64)(hi - lo);
+            }
+        }
+        if (s1) mq_atomic_add_i128(parts + 5 * q + 0, s1);
+        if (tr) mq_atomic_add_i128(parts + 5 * q + 1, (i128)tr);
+        q++;
+    }
+}
+
+int mq_s1_trivial(pc_ctx* ctx, const MQPlan& P)
+{
+    std::vector<u64> pref(P.Q + 1, 0);
+    for (u32 q = 0; q < P.Q; q++) pref[q + 1] = pref[q] + P.hq[q].nlim;
+    PC_TRY(buf_reserve(ctx, ctx->mq_pref, (P.Q + 1) * sizeof(u64)));
+    PC_CUDA(ctx, cudaMemcpyAsync(ctx->mq_pref.p, pref.data(), (P.Q + 1) * sizeof(u64), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    if (pref[P.Q] == 0) return PC_OK;
+    const int g = ctx->sm_count * 8;
+    mq_s1_trivial_kernel<<<g, 256, 0, ctx->stream>>>(table_args(ctx), P.dq, ctx->mq_pref.as<u64>(), P.Q,
+                                                     ctx->T.phiT[5].as<u32>(), 2310, P.parts);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    return PC_OK;
+}
+
+// easy ranges of every (query, b), c < b <= min(a, E): pair g of query q is b = c + 1 + g - pref[q]
+__global__ void mq_easy_ranges_kernel(LeafArgs T, const MQ* qs, const u64* pref, u32 Q, EasyRange* rng, u32* nch)
+{
+    const u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= pref[Q]) return;
+    const u64 q = mq_find(pref, Q + 1, g);
+    const MQ m = qs[q];
+    const EasyRange r = easy_range(T, m.x, m.y, m.a, m.c + 1 + (g - pref[q]));
+    rng[g] = r;
+    nch[g] = (u32)easy_chunks(r, clust_chunk_for(m.x));
+}
+
+// every chunk of every (query, b), handed out to warps one at a time
+__global__ void mq_easy_kernel(LeafArgs T, const MQ* qs, const u64* pref, u32 Q, const EasyRange* rng,
+                               const u64* choff, u64 npairs, unsigned long long* queue, I128Pair* parts)
+{
+    const u32 lane = threadIdx.x & 31;
+    const u64 nchunks = choff[npairs];
+    for (;;) {
+        u64 ch = 0;
+        if (lane == 0) ch = atomicAdd(queue, 1ull);
+        ch = __shfl_sync(0xffffffffu, ch, 0);
+        if (ch >= nchunks) break;
+        const u64 g = mq_find(choff, npairs + 1, ch);   // the pair of the chunk
+        const u64 q = mq_find(pref, Q + 1, g);
+        const MQ m = qs[q];
+        const EasyRange r = rng[g];
+        i64 s = 0;
+        u32 n1 = 0, nr = 0, nrl = 0;
+        easy_chunk<false>(T, m.x, m.a, m.c + 1 + (g - pref[q]), r, ch - choff[g], clust_chunk_for(m.x), lane, s,
+                          n1, nr, nrl);
+        s = warp_sum_i64(s);
+        if (lane == 0 && s) mq_atomic_add_i128(parts + 5 * q + 2, (i128)s);
+    }
+}
+
+int mq_easy(pc_ctx* ctx, const MQPlan& P)
+{
+    std::vector<u64> pref(P.Q + 1, 0);
+    for (u32 q = 0; q < P.Q; q++) {
+        const MQ& m = P.hq[q];
+        const u64 top = pc_min(m.a, m.E);
+        pref[q + 1] = pref[q] + (top > m.c ? top - m.c : 0);
+    }
+    const u64 np = pref[P.Q];
+    if (np == 0) return PC_OK;
+    // layout of mq_e: pref (Q+1 u64) | ranges (np) | chunk counts (np u32) | chunk offsets (np+1 u64) | queue
+    const size_t o_rng = ((P.Q + 1) * sizeof(u64) + 15) / 16 * 16;
+    const size_t o_nch = o_rng + np * sizeof(EasyRange);
+    const size_t o_off = (o_nch + np * sizeof(u32) + 15) / 16 * 16;
+    const size_t o_q = (o_off + (np + 1) * sizeof(u64) + 15) / 16 * 16;
+    PC_TRY(buf_reserve(ctx, ctx->mq_e, o_q + 64));
+    unsigned char* base = ctx->mq_e.as<unsigned char>();
+    u64* dpref = (u64*)base;
+    EasyRange* rng = (EasyRange*)(base + o_rng);
+    u32* nch = (u32*)(base + o_nch);
+    u64* choff = (u64*)(base + o_off);
+    unsigned long long* queue = (unsigned long long*)(base + o_q);
+    PC_CUDA(ctx, cudaMemcpyAsync(dpref, pref.data(), (P.Q + 1) * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
+    PC_CUDA(ctx, cudaMemsetAsync(queue, 0, 64, ctx->stream));
+    const LeafArgs T = table_args(ctx);
+    mq_easy_ranges_kernel<<<(unsigned)((np + 255) / 256), 256, 0, ctx->stream>>>(T, P.dq, dpref, P.Q, rng, nch);
+    PC_LAUNCHED(ctx);
+    PC_TRY(scan_exclusive_u32_to_u64(ctx, nch, choff, np));
+    mq_easy_kernel<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(T, P.dq, dpref, P.Q, rng, choff, np, queue, P.parts);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches += 2;
+    return PC_OK;
 }

@@ -35,13 +35,22 @@ struct P2Args {
 // per prime.
 static constexpr u32 P2_COOP_P = 512;
 
-template <int NT>
-__global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A)
+// A launch over the segments of many queries (the batched form): item g is segment
+// g - qpref[q] of query q, with arguments qargs[q] (all with the same segment geometry).
+struct P2Multi {
+    const P2Args* qargs;
+    const u32* qpref;   // nq + 1 entries
+    u32 nq;
+    unsigned long long items;
+};
+
+template <int NT, bool MULTI>
+__global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A0, P2Multi M)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u32* bits = (u32*)smem_raw;
-    const u32 seg_words = A.seg_bytes >> 2;
-    const u32 nblk = A.seg_bytes >> 7;
+    const u32 seg_words = A0.seg_bytes >> 2;
+    const u32 nblk = A0.seg_bytes >> 7;
     u32* blk = bits + seg_words;
     u32* pre = blk + nblk;
     const u64* bits64 = (const u64*)bits;
@@ -50,14 +59,39 @@ __global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A)
     __shared__ u32 s_seg;
     __shared__ i128 red[32];
     const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    make_pattern_words(patw, A.k0);
+    make_pattern_words(patw, A0.k0);
+    __shared__ __align__(16) unsigned char sA_raw[MULTI ? sizeof(P2Args) : 16];
+    __shared__ u32 s_q;
+    u32 cur_q = ~0u;
 
     for (;;) {
-        if (tid == 0) s_seg = atomicAdd(A.queue, 1u);
+        if (tid == 0) s_seg = atomicAdd(A0.queue, 1u);
         __syncthreads();
-        const u64 s = s_seg;
+        u64 s = s_seg;
         __syncthreads();
-        if (s >= A.nseg) break;
+        if (MULTI) {
+            if (s >= M.items) break;
+            if (tid == 0) {   // the item's query: the last q with qpref[q] <= item
+                u32 lo = 0, hi = M.nq;
+                while (hi - lo > 1) {
+                    const u32 mid = (lo + hi) >> 1;
+                    if (M.qpref[mid] <= s) lo = mid; else hi = mid;
+                }
+                s_q = lo;
+            }
+            __syncthreads();
+            const u32 q = s_q;
+            if (q != cur_q) {
+                const u32* src = (const u32*)(M.qargs + q);
+                for (u32 k = tid; k < sizeof(P2Args) / 4; k += NT) ((u32*)sA_raw)[k] = src[k];
+                cur_q = q;
+                __syncthreads();
+            }
+            s -= M.qpref[q];
+        } else if (s >= A0.nseg) {
+            break;
+        }
+        const P2Args& A = MULTI ? *(const P2Args*)sA_raw : A0;
         const u64 L = s * A.span;
         fill_pattern(bits, seg_words, L, patw, A.k0);
         u32 ncl = 0;
@@ -276,13 +310,13 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     size_t smem = A.seg_bytes + (2 * (size_t)nblk + 2) * sizeof(u32);
     // the kernel's limit is shared by every host thread: set the device maximum
     cudaFuncAttributes fa;
-    PC_CUDA(ctx, cudaFuncGetAttributes(&fa, p2_sieve_kernel<512>));
+    PC_CUDA(ctx, cudaFuncGetAttributes(&fa, p2_sieve_kernel<512, false>));
     const size_t dyn_max = ctx->smem_optin - fa.sharedSizeBytes;
     if (smem > dyn_max) {
         pc_set_error(ctx, "p2 sieve: %zu bytes of shared memory per CTA", smem);
         return PC_EINVAL;
     }
-    cudaError_t e = cudaFuncSetAttribute(p2_sieve_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(p2_sieve_kernel<512, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)dyn_max);
     if (e != cudaSuccess) {
         pc_set_error(ctx, "p2 smem attribute: %s", cudaGetErrorString(e));
@@ -295,7 +329,7 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     if ((u64)ctas > A.nseg) ctas = (int)A.nseg;
     A.stat = ctx->dstat;
     PC_CUDA(ctx, cudaEventRecord(ctx->ev[4], ctx->stream));
-    p2_sieve_kernel<512><<<ctas, 512, smem, ctx->stream>>>(A);
+    p2_sieve_kernel<512, false><<<ctas, 512, smem, ctx->stream>>>(A, P2Multi{});
     PC_LAUNCHED(ctx);
     PC_CUDA(ctx, cudaEventRecord(ctx->ev[5], ctx->stream));
     ctx->p2_timed = true;
@@ -321,5 +355,144 @@ int p2_constant(pc_ctx* ctx, u64 x, u64 y, u64 a, i128* out)
     i128 n = (i128)(K - a);
     i128 sum_k1 = ((i128)K * (i128)(K - 1) - (i128)a * (i128)(a - (a ? 1 : 0))) / 2;   // sum_{k=a+1}^{K} (k-1)
     *out = n * (i128)(B - 1) - sum_k1;
+    return PC_OK;
+}
+
+// ------------------------------------------------------- many queries at once
+// P2 of every query of a batch: one sieve launch over the segments of all their
+// intervals [0, z], then a warp per query for its carries and the closed-form part.
+
+// query q: sum_s acc[s] + tally[s] * phi(L_s - 1, B) + (K - a)(B - 1) - sum_{k=a+1}^{K} (k - 1)
+__global__ void mq_p2_combine_kernel(const P2Args* qa, const MQ* qs, u32 Q, I128Pair* parts)
+{
+    const u32 lane = threadIdx.x & 31;
+    const u64 q = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= Q) return;
+    const P2Args& A = qa[q];
+    const MQ m = qs[q];
+    if (m.K <= m.a || A.nseg == 0) return;
+    u64 carry = 0;
+    i128 dot = 0;
+    for (u64 base = 0; base < A.nseg; base += 32) {
+        const u64 s = base + lane;
+        const u64 v = s < A.nseg ? (u64)A.cnt[s] : 0;
+        u64 incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (s < A.nseg) dot += load_i128(A.acc + s) + (i128)A.tally[s] * (i128)(carry + incl - v);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    dot = warp_sum_i128(dot);
+    if (lane == 0) {
+        const i128 K = (i128)m.K, a = (i128)m.a;
+        dot += (K - a) * (i128)(m.B - 1) - (K * (K - 1) - a * (a ? a - 1 : 0)) / 2;
+        store_i128(parts + 5 * q + 4, dot);
+    }
+}
+
+// pi(x) = S1 + S2_triv + S2_easy + S2_hard + a - 1 - P2 for every query
+__global__ void mq_final_kernel(const MQ* qs, u32 Q, const I128Pair* parts, u64* out, int* bad)
+{
+    const u32 q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
+    const I128Pair* pq = parts + 5 * q;
+    const i128 pi = load_i128(pq) + load_i128(pq + 1) + load_i128(pq + 2) + load_i128(pq + 3) + (i128)qs[q].a - 1 -
+                    load_i128(pq + 4);
+    if (pi < 0 || (pi >> 64) != 0) *bad = 1;
+    out[q] = (u64)pi;
+}
+
+int mq_final(pc_ctx* ctx, const MQPlan& P, u64* d_out, int* d_bad)
+{
+    mq_final_kernel<<<(P.Q + 127) / 128, 128, 0, ctx->stream>>>(P.dq, P.Q, P.parts, d_out, d_bad);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    return PC_OK;
+}
+
+int mq_p2(pc_ctx* ctx, const MQPlan& P)
+{
+    const u32 Q = P.Q;
+    P2Args T{};
+    T.k0 = 5;
+    T.seg_bytes = 32768;
+    T.span = 30ull * T.seg_bytes;
+    T.pit = ctx->T.pi();
+    T.primes = ctx->T.primes.as<u32>();
+    T.primes_rcp = ctx->T.primes_rcp.as<u64>();
+    u64 v2[2] = {P2_COOP_P - 1, T.seg_bytes / 8}, pv2[2];
+    PC_TRY(tables_pi_values(ctx, v2, pv2, 2));
+    std::vector<u64> spref(Q + 1, 0);
+    for (u32 q = 0; q < Q; q++) {
+        const MQ& m = P.hq[q];
+        const bool work = m.c == 5 && m.K > m.a && m.B >= 5;
+        spref[q + 1] = spref[q] + (work ? m.z / T.span + 1 : 0);
+    }
+    const u64 S = spref[Q];
+    if (S >> 32) {
+        pc_set_error(ctx, "batch: %llu P2 segments", (unsigned long long)S);
+        return PC_EOVERFLOW;
+    }
+    // mq_p: per-query arguments (Q P2Args) | ipref (Q+1 u32) | cnt, tally (S u32 each) |
+    // acc (S I128Pair) | queue (64 B)
+    auto al = [](size_t v) { return (v + 15) / 16 * 16; };
+    const size_t o_ip = al(Q * sizeof(P2Args));
+    const size_t o_cnt = o_ip + al((Q + 1) * 4), o_tl = o_cnt + al(S * 4), o_acc = o_tl + al(S * 4);
+    const size_t o_q = o_acc + al(S * sizeof(I128Pair)), total = o_q + 64;
+    PC_TRY(buf_reserve(ctx, ctx->mq_p, total));
+    unsigned char* base = ctx->mq_p.as<unsigned char>();
+    P2Args* d_qa = (P2Args*)base;
+    u32* d_ipref = (u32*)(base + o_ip);
+    u32* d_cnt = (u32*)(base + o_cnt);
+    u32* d_tally = (u32*)(base + o_tl);
+    I128Pair* d_acc = (I128Pair*)(base + o_acc);
+    u32* d_queue = (u32*)(base + o_q);
+    std::vector<P2Args> qa(Q, T);
+    std::vector<u32> ipref(Q + 1);
+    for (u32 q = 0; q <= Q; q++) ipref[q] = (u32)spref[q];
+    for (u32 q = 0; q < Q; q++) {
+        const MQ& m = P.hq[q];
+        P2Args& A = qa[q];
+        A.x = m.x;
+        A.y = m.y;
+        A.z = m.z;
+        A.r = pc_isqrt(m.x);
+        A.B = (u32)m.B;
+        A.b_mid = (u32)pc_min(pc_max(pv2[0] + 1, (u64)A.k0 + 1), m.B + 1);
+        A.b_big = (u32)pc_min(pc_max(pv2[1] + 1, (u64)A.b_mid), m.B + 1);
+        A.nseg = spref[q + 1] - spref[q];
+        A.cnt = d_cnt + spref[q];
+        A.tally = d_tally + spref[q];
+        A.acc = d_acc + spref[q];
+        A.queue = d_queue;
+        A.stat = nullptr;
+    }
+    cudaStream_t st = ctx->stream;
+    PC_CUDA(ctx, cudaMemcpyAsync(d_qa, qa.data(), Q * sizeof(P2Args), cudaMemcpyHostToDevice, st));
+    PC_CUDA(ctx, cudaMemcpyAsync(d_ipref, ipref.data(), (Q + 1) * 4, cudaMemcpyHostToDevice, st));
+    PC_CUDA(ctx, cudaMemsetAsync(d_queue, 0, 64, st));
+    if (S) {
+        const u32 nblk = T.seg_bytes >> 7;
+        const size_t smem = T.seg_bytes + (2 * (size_t)nblk + 2) * sizeof(u32);
+        cudaFuncAttributes fa;
+        PC_CUDA(ctx, cudaFuncGetAttributes(&fa, p2_sieve_kernel<512, true>));
+        const size_t dyn_max = ctx->smem_optin - fa.sharedSizeBytes;
+        if (smem > dyn_max) return PC_EINVAL;
+        PC_CUDA(ctx, cudaFuncSetAttribute(p2_sieve_kernel<512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)dyn_max));
+        int per_sm = (int)(ctx->smem_optin / (smem + 4096));
+        if (per_sm < 1) per_sm = 1;
+        if (per_sm > 4) per_sm = 4;
+        const u64 ctas = pc_min((u64)ctx->sm_count * per_sm, S);
+        T.queue = d_queue;
+        T.nseg = 0;
+        p2_sieve_kernel<512, true><<<(unsigned)ctas, 512, smem, st>>>(T, P2Multi{d_qa, d_ipref, Q, S});
+        PC_LAUNCHED(ctx);
+    }
+    mq_p2_combine_kernel<<<(unsigned)((Q * 32 + 255) / 256), 256, 0, st>>>(d_qa, P.dq, Q, P.parts);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches += 2;
     return PC_OK;
 }
