@@ -261,7 +261,6 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
         const u64 end = pc_min(r.i1, start + per);
         if (start < end) {
             const u64 qlast = A.primes[end - 1];
-            const float xpf = (float)xp;
             for (u64 i = start; i < end;) {
                 const u64 u = div_rcp(xp, A.primes[i], A.primes_rcp[i]);
                 u64 l, pl = 0, w = 0, bits = 0;
@@ -291,17 +290,8 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
                             pl = A.primes[l];
                         }
                     }
-                    // the run: primes q' <= (x/p_b) / p_l.  The quotient is estimated in
-                    // single precision and made exact with integer remainders.
-                    const float rc = __frcp_rn((float)pl);
-                    i64 qb = (i64)(xpf * rc);
-                    i64 rem = (i64)xp - qb * (i64)pl;
-                    const i64 d = (i64)floorf((float)rem * rc);
-                    qb += d;
-                    rem -= d * (i64)pl;
-                    while (rem < 0) { qb--; rem += (i64)pl; }
-                    while (rem >= (i64)pl) { qb++; rem -= (i64)pl; }
-                    const u64 bound = (u64)qb;
+                    // the run: primes q' <= (x/p_b) / p_l, by the reciprocal of p_l (its index is l)
+                    const u64 bound = div_rcp(xp, pl, A.primes_rcp[l]);
                     u64 pb;
                     n = bound >= qlast ? end - i
                                        : (SAMPLED ? pi_sampled(A, bound, &pb) : pi_lookup(A.pit, bound)) - i + 1;
@@ -314,9 +304,9 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
         }
         return;
     }
-    const u64 start = r.i0 + c * EASY_CHUNK;
-    const u64 end = pc_min(r.im, start + EASY_CHUNK);
-    for (u64 i = start + lane; i < end; i += 32) {
+    const u32 start = (u32)(r.i0 + c * EASY_CHUNK);   // list and prime indices are below 2^32
+    const u32 end = (u32)pc_min(r.im, (u64)start + EASY_CHUNK);
+    for (u32 i = start + lane; i < end; i += 32) {
         u64 m, v;
         bool neg = true;
         if (r.src) {

@@ -19,16 +19,19 @@ __device__ __forceinline__ u64 coprime30_at_or_after(u64 k0)
 
 // Cooperative cross-off of the multiples k*p, k >= kstart, k coprime to 30,
 // inside the segment, by `nt` threads (t = 0..nt-1, nt a multiple of 8).
-// Each thread handles one residue class j and every (nt/8)-th wheel round.
+// Each thread handles one residue class j and every (nt/8)-th wheel round;
+// consecutive threads take one class in consecutive rounds, p bytes apart (a
+// warp of 256 or more threads: 32 rounds of one class), so that they spread
+// over the banks instead of crowding into the words of one round.
 // NEWLY(bitpos) is invoked for every bit that was set before this call
 // cleared it (bit position relative to the segment).
 template <class F>
 __device__ __forceinline__ u32 cross_off_coop(u32* bits, u32 seg_bytes, u64 L, u32 p, u64 kstart,
                                                int t, int nt, F&& newly)
 {
-    const int j = t & 7;
     const u32 rounds = (u32)nt >> 3;
-    const u32 o = (u32)t >> 3;
+    const int j = (u32)t / rounds;
+    const u32 o = (u32)t % rounds;
     const u32 rj = r8(j);
     const u64 q0 = kstart / 30;
     const u32 pr = p * rj;                 // p < 2^27 here, so no overflow
@@ -37,13 +40,13 @@ __device__ __forceinline__ u32 cross_off_coop(u32* bits, u32 seg_bytes, u64 L, u
     // byte(q) = p*q + pr/30 - L/30 for k = 30*q + rj
     u64 q = q0 + o;
     if (30 * q + rj < kstart) q += rounds;
-    u64 byte64 = (u64)p * q + pr / 30;
-    if (byte64 < Lb) return 0;             // cannot happen for kstart*p >= L
-    byte64 -= Lb;
-    const u64 step = (u64)p * rounds;
+    const u64 byte64 = (u64)p * q + pr / 30;
+    if (byte64 < Lb || byte64 - Lb >= seg_bytes) return 0;   // the first cannot happen for kstart*p >= L
+    // byte offsets inside the segment in 32 bits: below seg_bytes + step < 2^32
+    const u32 step = p * rounds;
     u32 n = 0;
-    for (; byte64 < seg_bytes; byte64 += step) {
-        u32 pos = ((u32)byte64 << 3) + bit;
+    for (u32 by = (u32)(byte64 - Lb); by < seg_bytes; by += step) {
+        u32 pos = (by << 3) + bit;
         u32 mask = 1u << (pos & 31);
         u32 old = atomicAnd(&bits[pos >> 5], ~mask);
         if (old & mask) newly(pos);
@@ -66,9 +69,9 @@ __device__ __forceinline__ u32 cross_off_class(u32* bits, u32 seg_bytes, u64 L, 
     const u32 bit = idx30(pr % 30);
     const u64 byte64 = (u64)p * q + pr / 30;
     const u64 Lb = L / 30;
-    if (byte64 < Lb) return 0;             // cannot happen for kstart*p >= L
+    if (byte64 < Lb || byte64 - Lb >= seg_bytes) return 0;   // the first cannot happen for kstart*p >= L
     u32 n = 0;
-    for (u64 by = byte64 - Lb; by < seg_bytes; by += p, n++) {
+    for (u64 by = byte64 - Lb; by < seg_bytes; by += p, n++) {   // 64-bit: p may be near 2^32
         const u32 pos = ((u32)by << 3) + bit;
         const u32 mask = 1u << (pos & 31);
         const u32 old = atomicAnd(&bits[pos >> 5], ~mask);

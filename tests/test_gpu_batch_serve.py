@@ -108,6 +108,34 @@ def test_server_results_equal_alone(alone):
             assert by_tag[i]["value"] == want
 
 
+def test_server_results_equal_alone_up_to_1e16(alone):
+    # the served workload's mix (80 % pi(x), 20 % phi(x, a)) with x up to 10^16
+    trace = inputs.served_trace(80, rate_per_s=4000.0, seed=23, lo_exp=9.0, hi_exp=16.0, a_hi=5000)
+    with pc.Context(0, streams=8) as cx:
+        with pc.Server(cx, x_max=10 ** 16, a_max=5000) as srv:
+            for i, r in enumerate(trace):
+                srv.submit(pc.PC_QUERY_PHI if r["kind"] == "phi" else pc.PC_QUERY_PI, r["x"], r["a"], tag=i)
+            res = _drain(srv, len(trace))
+            st = srv.stats()
+    assert st["completed"] == len(trace) and st["failed"] == 0
+    by_tag = {r["tag"]: r for r in res}
+    for i, r in enumerate(trace):
+        want = alone.phi(r["x"], r["a"]) if r["kind"] == "phi" else alone.pi_count(r["x"])
+        assert by_tag[i]["status"] == 0 and by_tag[i]["value"] == want, (r, by_tag[i])
+
+
+def test_batch_across_the_schedule_boundary(alone, pi_pow10):
+    # queries on both sides of the batched schedule's limit (1e16) and of the table
+    # cut-over (2^20), in one call; every result equal to the query alone and to Table 1
+    xs = inputs.log_uniform_x(120, 6.0, 16.6, seed=29)
+    xs += [10 ** n for n in range(6, 17)] + [(1 << 20) - 1, 1 << 20, 10 ** 16 - 1, 10 ** 16 + 1]
+    with pc.Context(0) as cx:
+        got = cx.pi_count_batch(xs)
+    assert got == [alone.pi_count(x) for x in xs]
+    for n in range(6, 17):
+        assert got[xs.index(10 ** n)] == pi_pow10[n], n
+
+
 def test_server_memory_budget_admits_one_at_a_time():
     xs = [10 ** 12 + 7919 * k for k in range(12)]
     with pc.Context(0, streams=8) as cx:
