@@ -380,7 +380,8 @@ def run_batch(local, n, streams, seed=0):
         t0 = time.perf_counter()
         cx.autotune(min(xs), max(xs))              # alpha and segment size per decade
         t_tune = time.perf_counter() - t0
-        tuned = {"1e%d" % (d - 1): cx.tuned(3 * 10 ** (d - 1)) for d in range(len(str(min(xs))), len(str(max(xs))) + 1)}
+        tuned = {"1e%d" % (d - 1): cx.tuned(3 * 10 ** (d - 1)) + (cx.tuned_ctas(3 * 10 ** (d - 1)),)
+                 for d in range(len(str(min(xs))), len(str(max(xs))) + 1)}
         cx.pi_count_batch(xs)                      # builds and warms the shared tables
         t0 = time.perf_counter()
         got = cx.pi_count_batch(xs)
@@ -395,7 +396,7 @@ def run_batch(local, n, streams, seed=0):
     return {"queries": n, "x": "floor(10^e), e ~ U(8, 15), numpy default_rng(%d)" % seed, "x_sha256": sha,
             "slots": streams, "batch_s": tb, "batch_qps": n / tb, "plain_loop_s": tl, "plain_qps": n / tl,
             "speedup": tl / tb, "bit_exact": True, "gpu_launches": launches,
-            "autotune_s": t_tune, "tuned_alpha_seg_per_decade": tuned}
+            "autotune_s": t_tune, "tuned_alpha_seg_ctas_per_decade": tuned}
 
 
 def run_serve(local, n, rate, streams, lo_exp=9.0, hi_exp=17.0, check=64, policy=0):

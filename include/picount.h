@@ -288,6 +288,12 @@ void pc_server_destroy(pc_server* s);
 #define PC_NOALLOC_SEG_SPAN 983040   /* integers per segment (32 KiB, mod-30 wheel) */
 int pc_p2_noalloc(uint64_t x, uint64_t y, const uint32_t* primes, uint64_t n_primes, uint64_t* out, void* stream);
 
+/* The resident CTAs per SM of the hard-leaf sieve that pi(x) calls use for x's decade:
+ * the autotuned value (pc_autotune tries the most that fit, 2, 4 and 6 after choosing alpha
+ * and the segment size), else 0 = as many as registers and shared memory allow (or the
+ * context's ctas_per_sm when set). */
+int pc_tuned_ctas(pc_ctx* ctx, uint64_t x, uint32_t* ctas_per_sm);
+
 /* Counters of the last successful call. */
 int pc_last_stats(pc_ctx* ctx, pc_stats* out);
 

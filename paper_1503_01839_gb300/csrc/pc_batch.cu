@@ -45,6 +45,7 @@ int workers_ensure(pc_ctx* ctx, int n)
         w->params = ctx->params;
         memcpy(w->tuned_alpha, ctx->tuned_alpha, sizeof(ctx->tuned_alpha));
         memcpy(w->tuned_seg, ctx->tuned_seg, sizeof(ctx->tuned_seg));
+        memcpy(w->tuned_ctas, ctx->tuned_ctas, sizeof(ctx->tuned_ctas));
     }
     return PC_OK;
 }
@@ -625,7 +626,48 @@ extern "C" int pc_autotune(pc_ctx* ctx, uint64_t x_lo, uint64_t x_hi, uint32_t r
         }
         ctx->tuned_alpha[d] = fixed_alpha ? 0 : best_a;
         ctx->tuned_seg[d] = best_s;
+        // then the resident CTAs per SM of the hard-leaf sieve at that alpha and segment size
+        ctx->tuned_ctas[d] = 0;
+        if (!ctx->params.ctas_per_sm) {
+            const u32 ctas[4] = {0, 2, 4, 6};
+            double best_c = 1e300;
+            u32 best_k = 0;
+            for (u32 ci = 0; ci < 4; ci++) {
+                ctx->tuned_ctas[d] = ctas[ci];
+                double ms = 1e300;
+                for (u32 r = 0; r <= reps; r++) {
+                    const auto t0 = std::chrono::steady_clock::now();
+                    u64 v = 0;
+                    memset(&ctx->stats, 0, sizeof(ctx->stats));
+                    PC_TRY(pi_count_impl(ctx, x, best_a, &v));
+                    const double dt =
+                        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+                    if (!have) {   // a fixed alpha none of the candidates matched: nothing timed yet
+                        want = v;
+                        have = true;
+                    } else if (v != want) {
+                        ctx->tuned_ctas[d] = 0;
+                        pc_set_error(ctx, "autotune: pi(%llu) differs between settings (alpha %u, segment %u, %u CTAs per SM)",
+                                     (unsigned long long)x, best_a, best_s, ctas[ci]);
+                        return PC_EOVERFLOW;
+                    }
+                    if (r && dt < ms) ms = dt;
+                }
+                if (ms < best_c) {
+                    best_c = ms;
+                    best_k = ctas[ci];
+                }
+            }
+            ctx->tuned_ctas[d] = best_k;
+        }
     }
+    return PC_OK;
+}
+
+extern "C" int pc_tuned_ctas(pc_ctx* ctx, uint64_t x, uint32_t* ctas_per_sm)
+{
+    if (!ctx || !ctas_per_sm) return PC_EINVAL;
+    *ctas_per_sm = ctx->params.ctas_per_sm ? ctx->params.ctas_per_sm : ctx->tuned_ctas[decimal_digits(x)];
     return PC_OK;
 }
 
@@ -648,7 +690,59 @@ extern "C" int pc_tuned(pc_ctx* ctx, uint64_t x, uint32_t* alpha, uint32_t* seg_
 //                          phi(v, b-1) = pi(v) - (b - 1) + 1, pi(v) from the pi table;
 //   otherwise:             phi(v, b-1) by the combinatorial algorithm (pc_phi),
 //                          these queries running concurrently on the worker slots.
-// The first value phi(m, c) is itself a pc_phi query.
+// v < p_b^2 holds exactly when p_b > iroot3(m), so the combinatorial terms are those of
+// c < b <= pi(iroot3 m).  The first value phi(m, c) is itself a pc_phi query.  The other
+// terms and the running differences are computed on the device.
+
+// term[b - c] for pi(iroot3 m) < b <= b_max (the ones below are the phi queries' values)
+__global__ void phi_terms_kernel(const u32* primes, PiTable pit, u64 m, u32 c, u64 b_max, u64 b3, u64* term)
+{
+    const u64 b = b3 + 1 + (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > b_max) return;
+    const u64 p = primes[b];
+    u64 t;
+    if (p > m) t = 0;
+    else if (p * p > m) t = 1;
+    else t = pi_lookup(pit, m / p) - b + 2;
+    term[b - c] = t;
+}
+
+// out[i] = first - sum_{1 <= j <= i} term[j], i < n, by one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) phi_sweep_kernel(const u64* term, u64 first, u64 n, u64* out)
+{
+    __shared__ u64 wsum[32];
+    __shared__ u64 s_run;
+    const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_run = 0;
+    __syncthreads();
+    for (u64 base = 0; base < n; base += 1024) {
+        const u64 i = base + threadIdx.x;
+        const u64 v = (i < n && i > 0) ? term[i] : 0;
+        u64 incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const u64 w = wsum[lane];
+            u64 wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const u64 t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            wsum[lane] = wi - w;
+        }
+        __syncthreads();
+        const u64 run = s_run;
+        if (i < n) out[i] = first - (run + wsum[wid] + incl);
+        __syncthreads();
+        if (threadIdx.x == 1023) s_run = run + wsum[wid] + incl;
+        __syncthreads();
+    }
+}
+
 int phi_starts(pc_ctx* ctx, u64 m, u32 c, u64 b_max, u64* out)
 {
     if (ctx->borrowed || c > b_max) return PC_EINVAL;
@@ -657,8 +751,6 @@ int phi_starts(pc_ctx* ctx, u64 m, u32 c, u64 b_max, u64* out)
         for (u64 i = 0; i < n; i++) out[i] = 0;
         return PC_OK;
     }
-    // p_1 .. p_{b_max} on the host
-    const u64 r = pc_isqrt(m);
     {
         // p_b <= b (ln b + ln ln b) for b >= 6 (Rosser); only sizes the prime table
         const double bb = (double)pc_max(b_max, (u64)6);
@@ -669,47 +761,26 @@ int phi_starts(pc_ctx* ctx, u64 m, u32 c, u64 b_max, u64* out)
         pc_set_error(ctx, "phi starts: %llu primes needed", (unsigned long long)b_max);
         return PC_EINVAL;
     }
-    std::vector<u32> P(b_max + 1);
-    PC_CUDA(ctx, cudaMemcpy(P.data(), ctx->T.primes.p, (b_max + 1) * sizeof(u32), cudaMemcpyDeviceToHost));
-    // classify every term
-    std::vector<u64> term(n, 0), lv, lb;
+    // the combinatorial terms: c < b <= b3 = min(pi(iroot3 m), b_max)
+    u64 b3 = 0;
+    {
+        const u64 v[1] = {pc_iroot3(m)};
+        PC_TRY(tables_pi_values(ctx, v, &b3, 1));
+        b3 = pc_min(pc_max(b3, (u64)c), b_max);
+    }
+    // p_0 .. p_{max(b3, c + 1)} (the table ends with a sentinel prime past b_max): the
+    // queries' arguments m / p_b, and p_a, p_{a+1} to size their tables
+    const u64 np = pc_max(b3, (u64)c + 1) + 1;
+    std::vector<u32> P(np);
+    PC_CUDA(ctx, cudaMemcpy(P.data(), ctx->T.primes.p, np * sizeof(u32), cudaMemcpyDeviceToHost));
     std::vector<Query> q;
-    std::vector<u64> qb;
     q.push_back(Query{PC_QUERY_PHI, m, c});   // phi(m, c)
-    qb.push_back(0);
-    for (u64 b = (u64)c + 1; b <= b_max; b++) {
-        const u64 p = P[b];
-        if (p > m) {
-            term[b - c] = 0;
-        } else if (p > r) {
-            term[b - c] = 1;
-        } else {
-            const u64 v = m / p;
-            if (v < p * p) {
-                lv.push_back(v);
-                lb.push_back(b);
-            } else {
-                q.push_back(Query{PC_QUERY_PHI, v, b - 1});
-                qb.push_back(b);
-            }
-        }
-    }
-    // Legendre terms from the pi table
-    if (!lv.empty()) {
-        u64 vmax = 0;
-        for (u64 v : lv) vmax = pc_max(vmax, v);
-        PC_TRY(tables_ensure(ctx, vmax, 64, 0, 7));
-        std::vector<u64> pv(lv.size());
-        PC_TRY(tables_pi_many(ctx, lv.data(), pv.data(), lv.size()));
-        for (size_t i = 0; i < lv.size(); i++) term[lb[i] - c] = pv[i] - lb[i] + 2;
-    }
-    // combinatorial terms, concurrently
+    for (u64 b = (u64)c + 1; b <= b3; b++) q.push_back(Query{PC_QUERY_PHI, m / P[b], b - 1});
     TableNeeds N;
     for (const Query& qq : q) {
         const u64 a = qq.a;
         if (a == 0) continue;
-        const u64 pa = P[a], pa1 = a + 1 <= b_max ? P[a + 1] : ~0ull;
-        needs_phi(ctx, qq.x, a, pa, pa1 == ~0ull ? pc_isqrt(qq.x) + 1 : pa1, N);
+        needs_phi(ctx, qq.x, a, P[a], P[a + 1], N);   // a + 1 <= max(b3, c + 1)
     }
     PC_TRY(build_needs(ctx, N));
     std::vector<u64> qv(q.size(), 0);
@@ -717,9 +788,22 @@ int phi_starts(pc_ctx* ctx, u64 m, u32 c, u64 b_max, u64* out)
     const int rq = run_queries(ctx, q, qv);
     ctx->stats = keep;
     PC_TRY(rq);
-    for (size_t i = 1; i < q.size(); i++) term[qb[i] - c] = qv[i];
-    out[0] = qv[0];
-    for (u64 i = 1; i < n; i++) out[i] = out[i - 1] - term[i];
+    // term[b - c]: the queries' values for b <= b3, the rest on the device; then the sweep
+    PC_TRY(buf_reserve(ctx, ctx->misc, 2 * n * sizeof(u64) + 64));
+    u64* d_term = ctx->misc.as<u64>();
+    u64* d_out = d_term + n;
+    if (b3 > c)
+        PC_CUDA(ctx, cudaMemcpyAsync(d_term + 1, qv.data() + 1, (b3 - c) * sizeof(u64), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    if (b_max > b3) {
+        phi_terms_kernel<<<(unsigned)((b_max - b3 + 255) / 256), 256, 0, ctx->stream>>>(
+            ctx->T.primes.as<u32>(), ctx->T.pi(), m, c, b_max, b3, d_term);
+        PC_LAUNCHED(ctx);
+    }
+    phi_sweep_kernel<<<1, 1024, 0, ctx->stream>>>(d_term, qv[0], n, d_out);
+    PC_LAUNCHED(ctx);
+    PC_CUDA(ctx, cudaMemcpyAsync(out, d_out, n * sizeof(u64), cudaMemcpyDeviceToHost, ctx->stream));
+    PC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return PC_OK;
 }
 

@@ -3,7 +3,9 @@
 // pi(x) = S1 + S2_triv + S2_easy + S2_hard + a - 1 - P2(x, a),  a = pi(y),
 // y = min(alpha * iroot3(x), isqrt(x)) (Section 2: y_max = alpha x^(1/3));
 // with y >= x^(1/3) the third partial sum P3 vanishes.  Every part is an
-// exact integer computed on the GPU; the host only adds the five i128 parts.
+// exact integer computed on the GPU; the host adds the five i128 parts and a - 1.
+// (The host also picks y, z and the launch sizes, and reads back the handful of
+// table values, such as pi(y), that size them.)
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -11,7 +13,6 @@
 
 #include "pc_internal.h"
 
-int p2_constant(pc_ctx* ctx, u64 x, u64 y, u64 a, i128* out);
 
 static const char* kVersion = "picount-gb300 0.1 (sm_103a)";
 
@@ -271,13 +272,7 @@ static int leaf_parts(pc_ctx* ctx, u64 x, u64 y, u32 c, u64 a, bool want_p2, i12
         PC_TRY(sync_timed(ctx, &ctx->stats.ms_p2, t));
     }
     PC_TRY(read_slots(ctx, 5, parts));
-    if (want_p2) {
-        i128 k;
-        PC_TRY(p2_constant(ctx, x, y, a, &k));
-        parts[4] += k;
-    } else {
-        parts[4] = 0;
-    }
+    if (!want_p2) parts[4] = 0;
     if (a_out) *a_out = a;
     return PC_OK;
 }
@@ -373,10 +368,8 @@ extern "C" int pc_p2(pc_ctx* ctx, uint64_t x, uint64_t y, uint64_t* out)
     I128Pair* d;
     PC_TRY(result_slots(ctx, 1, &d));
     PC_TRY(run_p2(ctx, x, y, pv[0], d));
-    i128 v, k;
+    i128 v;
     PC_TRY(read_slots(ctx, 1, &v));
-    PC_TRY(p2_constant(ctx, x, y, pv[0], &k));
-    v += k;
     if (v < 0 || (v >> 64) != 0) return PC_EOVERFLOW;
     *out = (uint64_t)v;
     ctx->stats.ms_p2 = t.ms();
@@ -398,6 +391,7 @@ int pi_count_impl(pc_ctx* ctx, u64 x, u32 alpha, u64* out)
     }
     if (alpha == 0) alpha = choose_alpha(ctx, x);
     ctx->seg_call = choose_seg(ctx, x);
+    ctx->ctas_call = ctx->params.ctas_per_sm ? 0 : ctx->tuned_ctas[decimal_digits(x)];
     const u64 r = pc_isqrt(x);
     u64 y = (u64)alpha * pc_iroot3(x);
     if (y > r) y = r;
@@ -414,6 +408,7 @@ int pi_count_impl(pc_ctx* ctx, u64 x, u32 alpha, u64* out)
     u64 a = 0;
     const int rc = leaf_parts(ctx, x, y, c, 0, true, parts, &a);
     ctx->seg_call = 0;
+    ctx->ctas_call = 0;
     if (rc != PC_OK) return rc;
     i128 pi = parts[0] + parts[1] + parts[2] + parts[3] + (i128)a - 1 - parts[4];
     if (pi < 0 || (pi >> 64) != 0) {

@@ -1311,7 +1311,7 @@ static int choose_hard_kernel(pc_ctx* ctx, const HardArgs& A, size_t smem, void 
                                        {hard_sieve_kernel<512, 2, MULTI>, 512, 2},
                                        {hard_sieve_kernel<256, 4, MULTI>, 256, 4}};
     const int nt = 32 * (int)A.nw;
-    const int want = (int)ctx->params.ctas_per_sm;
+    const int want = (int)(ctx->params.ctas_per_sm ? ctx->params.ctas_per_sm : ctx->ctas_call);
     void (*kern)(HardArgs, MultiArgs) = nullptr;
     int per_sm = 0;
     for (const Variant& v : variants) {

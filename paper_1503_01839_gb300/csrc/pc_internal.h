@@ -121,6 +121,8 @@ struct pc_ctx {
     u32 tuned_alpha[21] = {0};
     u32 tuned_seg[21] = {0};
     u32 seg_call = 0;   // segment bytes chosen for the running pi(x) call (0 = default)
+    u32 tuned_ctas[21] = {0};   // autotuned resident CTAs per SM of the hard-leaf sieve (0 = most)
+    u32 ctas_call = 0;          // the value for the running call
     // device counters of the running call (easy leaves, runs, their leaves, P2 crossings),
     // beside the result slots; null outside a leaf-sum call
     unsigned long long* dstat = nullptr;

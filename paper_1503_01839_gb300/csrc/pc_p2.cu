@@ -44,8 +44,11 @@ struct P2Multi {
     unsigned long long items;
 };
 
+// Three resident CTAs per SM (at most 42 registers a thread, no spills): the barriers
+// between a segment's phases then leave other CTAs to issue (17.0 against 18.8 ms at
+// pi(10^18) with two CTAs, and 27.9 ms with the one the registers allow when unbounded)
 template <int NT, bool MULTI>
-__global__ void __launch_bounds__(NT) p2_sieve_kernel(P2Args A0, P2Multi M)
+__global__ void __launch_bounds__(NT, 3) p2_sieve_kernel(P2Args A0, P2Multi M)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u32* bits = (u32*)smem_raw;
@@ -261,6 +264,15 @@ __global__ void p2_lookup_kernel(u64 x, u64 y, u64 r, PiTable pit, I128Pair* out
     if (threadIdx.x == 0) store_i128(out, load_i128(out) + s);
 }
 
+// The constant part of P2, (K - a)(B - 1) - sum_{k=a+1}^{K} (k - 1), K = pi(isqrt x),
+// B = pi(isqrt z), added to *out: every pi(x/p_k) = phi(x/p_k, B) + B - 1 and pi(p_k) = k.
+__global__ void p2_constant_kernel(u64 K, u64 a, u64 B, I128Pair* out)
+{
+    const i128 n = (i128)(K - a);
+    const i128 sum_k1 = ((i128)K * (i128)(K - 1) - (i128)a * (i128)(a ? a - 1 : 0)) / 2;   // sum_{k=a+1}^{K} (k - 1)
+    store_i128(out, load_i128(out) + n * (i128)(B - 1) - sum_k1);
+}
+
 int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
 {
     const u64 r = pc_isqrt(x);
@@ -286,7 +298,10 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     A.k0 = B >= 5 ? 5 : (u32)B;
     // 32 KiB segments up to z = 2^30, 64 KiB beyond (measured on GB300: the small
     // segments win by a third at z ~ 1e8 and lose a few percent at z ~ 1.5e9)
-    A.seg_bytes = pc_seg_bytes(ctx, A.z < (1ull << 30) ? 32768 : 65536);
+#ifndef PC_P2_BIG
+#define PC_P2_BIG 65536
+#endif
+    A.seg_bytes = pc_seg_bytes(ctx, A.z < (1ull << 30) ? 32768 : PC_P2_BIG);
     A.span = 30ull * A.seg_bytes;
     {
         u64 v2[2] = {P2_COOP_P - 1, A.seg_bytes / 8}, pv2[2];
@@ -335,26 +350,9 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     ctx->p2_timed = true;
     p2_combine_kernel<<<1, 1024, 0, ctx->stream>>>(A, out);
     PC_LAUNCHED(ctx);
-    ctx->stats.kernel_launches += 2;
-    return PC_OK;
-}
-
-// constant part of P2: (K - a)(B - 1) - sum_{k=a+1}^{K} (k - 1), with the
-// same K = pi(isqrt x), B = pi(isqrt z) as run_p2 (host, exact)
-int p2_constant(pc_ctx* ctx, u64 x, u64 y, u64 a, i128* out)
-{
-    const u64 r = pc_isqrt(x);
-    *out = 0;
-    if (r <= y) return PC_OK;
-    const u64 z = x / y;
-    u64 vals[2] = {r, pc_isqrt(z)};
-    u64 pv[2];
-    PC_TRY(tables_pi_values(ctx, vals, pv, 2));
-    const u64 K = pv[0], B = pv[1];
-    if (K <= a || B < 3) return PC_OK;
-    i128 n = (i128)(K - a);
-    i128 sum_k1 = ((i128)K * (i128)(K - 1) - (i128)a * (i128)(a - (a ? 1 : 0))) / 2;   // sum_{k=a+1}^{K} (k-1)
-    *out = n * (i128)(B - 1) - sum_k1;
+    p2_constant_kernel<<<1, 1, 0, ctx->stream>>>(K, a, B, out);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches += 3;
     return PC_OK;
 }
 

@@ -171,6 +171,7 @@ def test_autotune_keeps_results(alone):
         after = {x: cx.tuned(x) for x in before}
         for x, (al, sb) in after.items():
             assert al >= 1 and sb in (16384, 32768, 65536)
+            assert cx.tuned_ctas(x) in (0, 2, 4, 6)   # resident CTAs per SM, tuned too
         xs = inputs.log_uniform_x(60, 9.0, 12.3, seed=31) + [10 ** 10, 10 ** 12]
         got = cx.pi_count_batch(xs)
         assert got == [alone.pi_count(x) for x in xs]
