@@ -86,6 +86,29 @@ __device__ __forceinline__ u64 div_rcp(u64 n, u64 d, u64 v)
 }
 PC_HD u64 pc_max(u64 a, u64 b) { return a > b ? a : b; }
 
+// floor(n / d) for d = low word of dv, v = high word = floor((2^(32+s) - 1) / d),
+// s = floor(log2 d), whenever the quotient is below 2^31.  v < 2^32 and
+// v > 2^(32+s)/d - 1, so n v / 2^(32+s) falls short of n/d by less than
+// n / 2^(32+s) < 2 (n/d) / 2^32 < 1: the estimate is the quotient or one less,
+// and one remainder test settles it.  Two 32x32 -> 64-bit products instead of
+// the 64-bit high product of div_rcp.
+__device__ __forceinline__ u32 div_dv(u64 n, u64 dv)
+{
+    const u32 d = (u32)dv, v = (u32)(dv >> 32);
+    const u64 lo = (u64)(u32)n * v;
+    const u64 hi = (u64)(u32)(n >> 32) * v + (lo >> 32);   // floor(n v / 2^32)
+    u32 q = (u32)(hi >> (31 - __clz(d)));
+    if (n - (u64)q * d >= d) q++;
+    return q;
+}
+PC_HD u64 pc_dv(u32 d)
+{
+    if (d == 0) return 0;
+    int s = 31;
+    while (!((d >> s) & 1u)) s--;
+    return (u64)d | ((((1ull << (32 + s)) - 1) / d) << 32);
+}
+
 // ----------------------------------------------------------- lookup tables
 // pi table: mod-30 bitset of the primes in [0, limit] (1 is cleared), one
 // record per 240 numbers: the 64-bit word and the number of set bits in all
@@ -120,6 +143,18 @@ __device__ __forceinline__ u64 pi_lookup(const PiTable& t, u64 v)
     const u32 e = 8 * (q30 & 7) + cntle30(v32 - 30 * q30);
     const uint4 q = __ldg((const uint4*)(t.rec + (q30 >> 3)));
     return small + q.z + __popcll(low_bits_top((u64)q.x | ((u64)q.y << 32), e));
+}
+
+// Odd-number pi table: record w covers [64w, 64w + 64); .x holds one bit per
+// odd number 64w + 2j + 1 (j = 0..31) that is prime, with bit 0 of record 0
+// (the number 1) standing for the prime 2, and .y = pi(64w - 1).  pi(u) for
+// 2 <= u <= limit is .y plus the bits of the odd numbers <= u: a shift, an
+// 8-byte load and one 32-bit popcount, with no division and no wheel residue.
+__device__ __forceinline__ u32 pi_odd(const uint2* t, u32 u)
+{
+    const uint2 r = __ldg(t + (u >> 6));
+    const u32 e = ((u & 63u) + 1u) >> 1;   // odd numbers <= u in the record, 0..32
+    return r.y + __popc(__funnelshift_lc(0u, r.x, 32u - e));   // r.x << (32 - e), 0 when e = 0
 }
 
 // rank structure over a plain bitset of [0, limit]: rank(v) = #set bits <= v.

@@ -58,6 +58,7 @@ struct Tables {
     u64 nprimes = 0;
     DevBuf primes;
     DevBuf primes_rcp;   // floor((2^64 - 1) / p_k), same indexing as primes
+    DevBuf primes_dv;    // p_k | floor((2^(32+s) - 1) / p_k) << 32, s = floor(log2 p_k) (div_dv)
     // squarefree m-list over [2, ml_limit] with lpf > p_cmin
     u64 ml_limit = 0;
     u32 ml_cmin = 99;
@@ -74,6 +75,9 @@ struct Tables {
     DevBuf samp;
     u32 samp_s = 0;
     u64 samp_limit = 0;
+    // odd-number pi table over [0, podd_limit] (pi_odd): one uint2 per 64 integers
+    DevBuf pi_odd;
+    u64 podd_limit = 0;
     // phi(., c) residue tables for the primorial of c (c = 0..7)
     DevBuf phiT[8];
     bool phiT_ok[8] = {false, false, false, false, false, false, false, false};

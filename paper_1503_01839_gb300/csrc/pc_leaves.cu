@@ -24,6 +24,8 @@ struct LeafArgs {
     MList ml;
     const u32* primes;
     const u64* primes_rcp;   // floor((2^64 - 1) / p_k)
+    const u64* primes_dv;    // p_k and its 32-bit reciprocal (div_dv)
+    const uint2* podd;       // odd-number pi table (pi_odd) over [0, y]
     u64 n_lim;   // list entries with m <= y: [0, n_lim)
     // easy-leaf gathers from the sampled table of Section 2.1 instead of the pi table
     const u32* samp;
@@ -64,6 +66,8 @@ static LeafArgs make_args(pc_ctx* ctx, const LeafProblem& P, u64 n_lim)
     A.ml = ctx->T.mlist();
     A.primes = ctx->T.primes.as<u32>();
     A.primes_rcp = ctx->T.primes_rcp.as<u64>();
+    A.primes_dv = ctx->T.primes_dv.as<u64>();
+    A.podd = ctx->T.pi_odd.as<uint2>();
     A.n_lim = n_lim;
     A.samp = ctx->T.samp.as<u32>();
     A.samp_s = ctx->T.samp_s;
@@ -245,9 +249,16 @@ __global__ void easy_chunk_map_kernel(u64 nb, const u64* choff, u32* cmap)
     for (u64 ch = choff[t]; ch < choff[t + 1]; ch++) cmap[ch] = (u32)t;
 }
 
+// How an easy leaf reads pi(u): from the popcount pi table (PI_REC), from the
+// sampled table of Section 2.1 (PI_SAMPLED), or from the odd-number table with
+// the 32-bit reciprocal divisions of div_dv (PI_ODD, for y < 2^29: every
+// quotient taken, u < y and the run bound (x/p_b)/p_l < 2.3 y, stays below 2^31).
+enum { PI_REC = 0, PI_SAMPLED = 1, PI_ODD = 2 };
+static constexpr u64 PI_ODD_Y = 1ull << 29;
+
 // One chunk of the easy leaves of p_b (query x, a): chunk c of range r, walked by the
 // 32 lanes of a warp; adds this lane's share of the sum to s.
-template <bool SAMPLED>
+template <int MODE>
 __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 b, const EasyRange& r, u64 c, u32 cc,
                                            u32 lane, i64& s, u32& n_one, u32& n_runs, u32& n_run_leaves)
 {
@@ -259,13 +270,29 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
         const u64 per = cc / 32;
         const u64 start = r.im + (c - nsp) * cc + lane * per;
         const u64 end = pc_min(r.i1, start + per);
-        if (start < end) {
-            const u64 qlast = A.primes[end - 1];
+        if (start >= end) return;
+        const u64 qlast = A.primes[end - 1];
+        if constexpr (MODE == PI_ODD) {
+            for (u32 i = (u32)start; i < (u32)end;) {
+                const u32 u = div_dv(xp, A.primes_dv[i]);
+                const u32 l = pi_odd(A.podd, u);   // u >= p_b >= 2
+                u32 n = 1;
+                if (i + 1 < (u32)end) {
+                    // the run: primes q' <= (x/p_b) / p_l; p_l and its reciprocal are record l
+                    const u32 bound = div_dv(xp, A.primes_dv[l]);
+                    n = bound >= qlast ? (u32)end - i : pi_odd(A.podd, bound) - i + 1;
+                }
+                s += (i64)n * ((i64)l - (i64)b + 2);
+                n_runs++;
+                n_run_leaves += n;
+                i += n;
+            }
+        } else {
             for (u64 i = start; i < end;) {
                 const u64 u = div_rcp(xp, A.primes[i], A.primes_rcp[i]);
                 u64 l, pl = 0, w = 0, bits = 0;
                 u32 hb0 = 0;
-                if (SAMPLED) {
+                if (MODE == PI_SAMPLED) {
                     l = pi_sampled(A, u, &pl);
                 } else {
                     // pi(u) from u's record (u >= p_b >= 13, so 2, 3 and 5 all count)
@@ -281,7 +308,7 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
                 }
                 u64 n = 1;
                 if (i + 1 < end) {
-                    if (!SAMPLED) {
+                    if (MODE == PI_REC) {
                         // p_l, the largest prime <= u, from the same record when it holds one
                         if (bits) {
                             const u32 hb = hb0 - __clzll((long long)bits);   // its bit in the record
@@ -294,7 +321,7 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
                     const u64 bound = div_rcp(xp, pl, A.primes_rcp[l]);
                     u64 pb;
                     n = bound >= qlast ? end - i
-                                       : (SAMPLED ? pi_sampled(A, bound, &pb) : pi_lookup(A.pit, bound)) - i + 1;
+                                       : (MODE == PI_SAMPLED ? pi_sampled(A, bound, &pb) : pi_lookup(A.pit, bound)) - i + 1;
                 }
                 s += (i64)n * ((i64)l - (i64)b + 2);
                 n_runs++;
@@ -306,6 +333,15 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
     }
     const u32 start = (u32)(r.i0 + c * EASY_CHUNK);   // list and prime indices are below 2^32
     const u32 end = (u32)pc_min(r.im, (u64)start + EASY_CHUNK);
+    if (MODE == PI_ODD && r.src) {
+        // m = q prime: every leaf adds pi(u) - b + 2
+        u64 sum = 0;
+        u32 k = 0;
+        for (u32 i = start + lane; i < end; i += 32, k++) sum += pi_odd(A.podd, div_dv(xp, A.primes_dv[i]));
+        s += (i64)sum - (i64)k * ((i64)b - 2);
+        n_one += k;
+        return;
+    }
     for (u32 i = start + lane; i < end; i += 32) {
         u64 m, v;
         bool neg = true;
@@ -323,9 +359,11 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
         // easy: p_b <= u < y < 2^32; for b > 3, u >= 7 and pi(u) counts 2, 3, 5
         const u32 u = (u32)div_rcp(xp, m, v);
         u64 piu;
-        if (SAMPLED) {
+        if (MODE == PI_SAMPLED) {
             u64 pv;
             piu = pi_sampled(A, u, &pv);
+        } else if (MODE == PI_ODD) {
+            piu = pi_odd(A.podd, u);   // u >= p_b >= 2
         } else {
             const u32 q30 = u / 30, w = q30 >> 3;
             const u32 e = 8 * (q30 & 7) + cntle30(u - 30 * q30);   // 0..64
@@ -340,9 +378,8 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
     }
 }
 
-// SAMPLED: read pi(u) from the sampled table instead of the popcount table
-// (a template parameter, so that the default instantiation carries no trace of it)
-template <bool SAMPLED>
+// MODE: how pi(u) is read (PI_REC, PI_SAMPLED, PI_ODD)
+template <int MODE>
 __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u64* choff, const u32* cmap,
                             u64 nchunks, unsigned long long* queue, I128Pair* part, unsigned long long* stat)
 {
@@ -358,7 +395,7 @@ __global__ void easy_kernel(LeafArgs A, u64 b_lo, const EasyRange* rng, const u6
         if (ch >= nchunks) break;
         const u64 t = cmap[ch];
         const EasyRange r = rng[t];
-        easy_chunk<SAMPLED>(A, A.x, A.a, b_lo + t, r, ch - choff[t], A.clust_chunk, lane, s, n_one, n_runs,
+        easy_chunk<MODE>(A, A.x, A.a, b_lo + t, r, ch - choff[t], A.clust_chunk, lane, s, n_one, n_runs,
                             n_run_leaves);
     }
     if (stat) {
@@ -406,12 +443,18 @@ int run_easy(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     PC_TRY(buf_reserve(ctx, ctx->queue, 64));
     PC_CUDA(ctx, cudaMemsetAsync(ctx->queue.p, 0, 64, ctx->stream));
     PC_CUDA(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
+    const EasyRange* rng = ctx->easy_rng.as<EasyRange>();
+    const u32* cmap = ctx->easy_cmap.as<u32>();
+    unsigned long long* queue = (unsigned long long*)ctx->queue.p;
     if (A.sampled)
-        easy_kernel<true><<<g, 256, 0, ctx->stream>>>(A, b_lo, ctx->easy_rng.as<EasyRange>(), choff, ctx->easy_cmap.as<u32>(), nchunks,
-                                            (unsigned long long*)ctx->queue.p, ctx->partials.as<I128Pair>(), ctx->dstat);
+        easy_kernel<PI_SAMPLED><<<g, 256, 0, ctx->stream>>>(A, b_lo, rng, choff, cmap, nchunks, queue,
+                                                            ctx->partials.as<I128Pair>(), ctx->dstat);
+    else if (P.y < PI_ODD_Y && ctx->T.podd_limit >= P.y)
+        easy_kernel<PI_ODD><<<g, 256, 0, ctx->stream>>>(A, b_lo, rng, choff, cmap, nchunks, queue,
+                                                        ctx->partials.as<I128Pair>(), ctx->dstat);
     else
-        easy_kernel<false><<<g, 256, 0, ctx->stream>>>(A, b_lo, ctx->easy_rng.as<EasyRange>(), choff, ctx->easy_cmap.as<u32>(), nchunks,
-                                            (unsigned long long*)ctx->queue.p, ctx->partials.as<I128Pair>(), ctx->dstat);
+        easy_kernel<PI_REC><<<g, 256, 0, ctx->stream>>>(A, b_lo, rng, choff, cmap, nchunks, queue,
+                                                        ctx->partials.as<I128Pair>(), ctx->dstat);
     PC_LAUNCHED(ctx);
     PC_CUDA(ctx, cudaEventRecord(ctx->ev[3], ctx->stream));
     ctx->easy_timed = true;
@@ -603,7 +646,7 @@ __global__ void mq_easy_kernel(LeafArgs T, const MQ* qs, const u64* pref, u32 Q,
         const EasyRange r = rng[g];
         i64 s = 0;
         u32 n1 = 0, nr = 0, nrl = 0;
-        easy_chunk<false>(T, m.x, m.a, m.c + 1 + (g - pref[q]), r, ch - choff[g], clust_chunk_for(m.x), lane, s,
+        easy_chunk<PI_ODD>(T, m.x, m.a, m.c + 1 + (g - pref[q]), r, ch - choff[g], clust_chunk_for(m.x), lane, s,
                           n1, nr, nrl);
         s = warp_sum_i64(s);
         if (lane == 0 && s) mq_atomic_add_i128(parts + 5 * q + 2, (i128)s);
@@ -620,6 +663,13 @@ int mq_easy(pc_ctx* ctx, const MQPlan& P)
     }
     const u64 np = pref[P.Q];
     if (np == 0) return PC_OK;
+    // the batch's x < 10^16 keeps y <= isqrt(x) < 2^29 (PI_ODD)
+    for (u32 q = 0; q < P.Q; q++)
+        if (P.hq[q].y >= PI_ODD_Y || P.hq[q].y > ctx->T.podd_limit) {
+            pc_set_error(ctx, "batched easy leaves: y = %llu beyond the odd-number pi table",
+                         (unsigned long long)P.hq[q].y);
+            return PC_EINVAL;
+        }
     // layout of mq_e: pref (Q+1 u64) | ranges (np) | chunk counts (np u32) | chunk offsets (np+1 u64) | queue
     const size_t o_rng = ((P.Q + 1) * sizeof(u64) + 15) / 16 * 16;
     const size_t o_nch = o_rng + np * sizeof(EasyRange);

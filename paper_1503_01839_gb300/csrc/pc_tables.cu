@@ -250,6 +250,45 @@ __global__ void reciprocal_kernel(const u32* d, u64 n, u64* v)
     if (i < n) v[i] = d[i] ? ~0ull / d[i] : 0;
 }
 
+// the 32-bit reciprocal records of div_dv
+__global__ void dv_kernel(const u32* d, u64 n, u64* dv)
+{
+    u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dv[i] = pc_dv(d[i]);
+}
+
+// odd-number pi table (pi_odd) over [0, 64 n): a thread per odd number 2t + 1,
+// a warp per record (blocks of 256 threads keep a record in one warp)
+__global__ void pi_odd_kernel(PiTable pit, u64 n, uint2* out)
+{
+    const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 w = t >> 5, v = 2 * t + 1;
+    bool prime = false;
+    if (v <= 5) {
+        prime = true;   // 1 stands for 2; 3 and 5
+    } else if (v <= pit.limit) {
+        const u32 r = (u32)(v % 30);
+        if (coprime30(r)) {
+            const u64 q30 = v / 30;
+            prime = (pit.rec[q30 >> 3].bits >> (8 * (q30 & 7) + idx30(r))) & 1;
+        }
+    }
+    const u32 bits = __ballot_sync(0xffffffffu, prime);
+    if ((threadIdx.x & 31) == 0 && w < n) out[w] = make_uint2(bits, w ? (u32)pi_lookup(pit, 64 * w - 1) : 0u);
+}
+
+static int build_pi_odd(pc_ctx* ctx, u64 limit)
+{
+    Tables& T = ctx->T;
+    const u64 n = limit / 64 + 1;
+    PC_TRY(buf_reserve(ctx, T.pi_odd, n * sizeof(uint2)));
+    pi_odd_kernel<<<(unsigned)((32 * n + 255) / 256), 256, 0, ctx->stream>>>(T.pi(), n, T.pi_odd.as<uint2>());
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    T.podd_limit = limit;
+    return PC_OK;
+}
+
 // ------------------------------------------------------------ phi tables
 __global__ void coprime_flags_kernel(u32 Q, u32 c, const u32* sp, u32* flags)
 {
@@ -347,7 +386,11 @@ static int build_primes(pc_ctx* ctx, u64 prime_limit)
     reciprocal_kernel<<<(unsigned)((n_out + 1 + 255) / 256), 256, 0, ctx->stream>>>(T.primes.as<u32>(), n_out + 1,
                                                                                    T.primes_rcp.as<u64>());
     PC_LAUNCHED(ctx);
-    ctx->stats.kernel_launches += 2;
+    PC_TRY(buf_reserve(ctx, T.primes_dv, (n_out + 2) * sizeof(u64)));
+    dv_kernel<<<(unsigned)((n_out + 1 + 255) / 256), 256, 0, ctx->stream>>>(T.primes.as<u32>(), n_out + 1,
+                                                                            T.primes_dv.as<u64>());
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches += 3;
     T.nprimes = np;
     T.prime_limit = prime_limit;
     return PC_OK;
@@ -536,7 +579,7 @@ int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 
     if (ctx->borrowed) {
         // a worker reads its parent's tables and must find them big enough
         if (T.n_small && pi_limit <= T.pi_limit && prime_limit <= T.prime_limit &&
-            (ml_limit == 0 || (ml_limit <= T.ml_limit && cmin >= T.ml_cmin &&
+            (ml_limit == 0 || (ml_limit <= T.ml_limit && cmin >= T.ml_cmin && ml_limit <= T.podd_limit &&
                                (ctx->params.pi_gather == 0 || ml_limit <= T.samp_limit))))
             return PC_OK;
         pc_set_error(ctx, "query needs tables beyond those prepared for the batch");
@@ -576,6 +619,8 @@ int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 
         PC_TRY(build_mlist(ctx, lim, cm));
         PC_TRY(build_sublists(ctx));
     }
+    // the odd-number pi table serves the easy leaves, whose u stays below the m-list limit y
+    if (ml_limit > 0 && T.ml_limit > T.podd_limit) PC_TRY(build_pi_odd(ctx, T.ml_limit));
     // the sampled table serves the easy leaves, whose u stays below the m-list limit y
     if (ctx->params.pi_gather == 1 && ml_limit > 0 && T.ml_limit > T.samp_limit)
         PC_TRY(build_sampled(ctx, T.ml_limit));
