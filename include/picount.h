@@ -71,6 +71,12 @@ typedef struct pc_params {
                              default); 1 = the sampled table of Section 2.1
                              (pi at every floor(log2 y)-th integer, then a walk
                              along the primes) */
+    uint32_t m_source;    /* how the list of squarefree m <= y (lpf > p_c, with
+                             lpf, mu and gpf) is built: 0 = a sieve of least and
+                             greatest prime factors per integer (the default);
+                             1 = the nested loops of Section 2.2 over products of
+                             distinct primes, mu = (-1)^(number of primes), with
+                             no per-integer table.  Both give the same list. */
 } pc_params;
 
 /* Counters and phase times of the last successful call. */

@@ -39,7 +39,7 @@ class PcI128(ctypes.Structure):
 class PcParams(ctypes.Structure):
     _fields_ = [("seg_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("threads", ctypes.c_uint32),
                 ("alpha", ctypes.c_uint32), ("c", ctypes.c_uint32), ("warp_bytes", ctypes.c_uint32),
-                ("streams", ctypes.c_uint32), ("pi_gather", ctypes.c_uint32)]
+                ("streams", ctypes.c_uint32), ("pi_gather", ctypes.c_uint32), ("m_source", ctypes.c_uint32)]
 
 
 class PcStats(ctypes.Structure):
@@ -143,9 +143,10 @@ class Context:
     """One library context (device tables + scratch) on one CUDA device."""
 
     def __init__(self, device: int = 0, seg_bytes: int = 0, ctas_per_sm: int = 0, threads: int = 0,
-                 alpha: int = 0, c: int = 0, warp_bytes: int = 0, streams: int = 0, pi_gather: int = 0):
+                 alpha: int = 0, c: int = 0, warp_bytes: int = 0, streams: int = 0, pi_gather: int = 0,
+                 m_source: int = 0):
         self._L = lib()
-        prm = PcParams(seg_bytes, ctas_per_sm, threads, alpha, c, warp_bytes, streams, pi_gather)
+        prm = PcParams(seg_bytes, ctas_per_sm, threads, alpha, c, warp_bytes, streams, pi_gather, m_source)
         h = ctypes.c_void_p()
         rc = self._L.pc_create(ctypes.byref(h), device, ctypes.byref(prm))
         if rc != PC_OK:

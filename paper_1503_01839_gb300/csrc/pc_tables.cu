@@ -508,6 +508,233 @@ static int build_sublists(pc_ctx* ctx)
     return rc;
 }
 
+// ------------------------------------------ m-list by nested loops (Section 2.2)
+// The same list without a table of least prime factors: the squarefree m <= Y with
+// lpf(m) > p_cmin are the products p_b1 p_b2 ... p_bn of distinct primes, cmin < b1 <
+// b2 < ... < bn, and mu(m) = (-1)^n.  They are enumerated level by level.  A prefix
+// P = p_b1 ... p_bk (P = 1 at level 0, with b_k read as cmin) owns the entries P p_j for
+// every prime index j > b_k with P p_j <= Y, each with lpf index b1 (j at level 0), gpf
+// index j and n = k + 1 factors; P p_j is a prefix of the next level when it still has
+// an entry, P p_j p_(j+1) <= Y.  A level with no prefixes ends the loops (at most 15
+// levels below 2^64, since 2 * 3 * ... * 53 > 2^64).  The entries are then placed in
+// ascending order through the rank bitset of the members: set, counted, and every entry
+// written at its rank.
+struct NestPrefix {
+    u64 P;     // product of the prefix's primes (1 at level 0)
+    u32 lpf;   // index of its least prime (unused at level 0)
+    u32 gi;    // index of its largest prime (cmin at level 0)
+    u32 nf;    // number of primes
+    u32 pad;
+};
+
+// children of each prefix: the j in (gi, J] with p_j p_(j+1) <= Y / P (a monotone test)
+__global__ void nest_children_kernel(const NestPrefix* lv, u32 n, const u32* primes, PiTable pit, u64 Y, u32* cnt)
+{
+    const u32 k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const NestPrefix q = lv[k];
+    const u64 R = Y / q.P;
+    // p_j^2 < p_j p_(j+1) <= R bounds j by pi(isqrt R)
+    u64 lo = q.gi, hi = pi_lookup(pit, pc_isqrt(R));   // the answer J lies in [gi, hi]
+    while (hi > lo) {
+        const u64 mid = lo + (hi - lo + 1) / 2;
+        if ((u64)primes[mid] * primes[mid + 1] <= R) lo = mid;
+        else hi = mid - 1;
+    }
+    cnt[k] = (u32)(lo - q.gi);
+}
+
+__global__ void nest_expand_kernel(const NestPrefix* lv, u32 n, const u32* off, const u32* primes, NestPrefix* next)
+{
+    const u32 k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const NestPrefix q = lv[k];
+    const u32 c = off[k + 1] - off[k];
+    for (u32 t = 0; t < c; t++) {
+        const u32 j = q.gi + 1 + t;
+        next[off[k] + t] = NestPrefix{q.P * primes[j], q.nf ? q.lpf : j, j, q.nf + 1, 0};
+    }
+}
+
+// entries of each prefix: the j in (gi, pi(Y / P)]
+__global__ void nest_entries_kernel(const NestPrefix* all, u64 n, PiTable pit, u64 Y, u32* cnt)
+{
+    const u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const u64 hi = pi_lookup(pit, Y / all[k].P);
+    cnt[k] = hi > all[k].gi ? (u32)(hi - all[k].gi) : 0u;
+}
+
+// entry g: its prefix (the last k with eoff[k] <= g), its prime index and its m
+__device__ __forceinline__ void nest_entry(const NestPrefix* all, u64 n, const u64* eoff, const u32* primes, u64 g,
+                                           NestPrefix& q, u32& j, u64& m)
+{
+    u64 lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const u64 mid = (lo + hi) >> 1;
+        if (eoff[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    q = all[lo];
+    j = q.gi + 1 + (u32)(g - eoff[lo]);
+    m = q.P * primes[j];
+}
+
+__global__ void nest_mark_kernel(const NestPrefix* all, u64 n, const u64* eoff, const u32* primes, u64* rbits)
+{
+    const u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= eoff[n]) return;
+    NestPrefix q;
+    u32 j;
+    u64 m;
+    nest_entry(all, n, eoff, primes, g, q, j, m);
+    atomicOr((unsigned long long*)&rbits[m >> 6], 1ull << (m & 63));
+}
+
+__global__ void nest_scatter_kernel(const NestPrefix* all, u64 n, const u64* eoff, const u32* primes,
+                                    const u64* rbits, const u32* rcnt, u32* mm, u32* minfo, u32* mgpf)
+{
+    const u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= eoff[n]) return;
+    NestPrefix q;
+    u32 j;
+    u64 m;
+    nest_entry(all, n, eoff, primes, g, q, j, m);
+    const u64 idx = rcnt[m >> 6] + __popcll(rbits[m >> 6] & ((1ull << (m & 63)) - 1));
+    mm[idx] = (u32)m;
+    minfo[idx] = ((q.nf ? q.lpf : j) << 1) | ((q.nf + 1) & 1u);   // mu = -1 for an odd count of primes
+    mgpf[idx] = j;
+}
+
+static int build_mlist_nested(pc_ctx* ctx, u64 Y, u32 cmin)
+{
+    Tables& T = ctx->T;
+    // the entries' largest primes reach Y / p_(cmin+1): the prime table must cover Y
+    if (T.prime_limit < Y) {
+        if (Y + 2048 > T.pi_limit) {
+            pc_set_error(ctx, "nested m-list: the pi table ends below %llu", (unsigned long long)(Y + 2048));
+            return PC_EINVAL;
+        }
+        PC_TRY(build_primes(ctx, Y));
+    }
+    const u32* primes = T.primes.as<u32>();
+    // the prefixes, level by level, appended to one array
+    std::vector<u32> level_n;
+    DevBuf all, nxt, cnt;
+    u64 n_all = 1, cap = 1024;
+    int rc = buf_reserve(ctx, all, cap * sizeof(NestPrefix));
+    if (rc) return rc;
+    {
+        const NestPrefix root{1, 0, cmin, 0, 0};
+        rc = cudaMemcpyAsync(all.p, &root, sizeof(root), cudaMemcpyHostToDevice, ctx->stream) == cudaSuccess
+                 ? PC_OK : PC_ECUDA;
+    }
+    u64 lv0 = 0, lvn = 1;   // the current level: all[lv0, lv0 + lvn)
+    int levels = 0;
+    while (rc == PC_OK && lvn > 0) {
+        if (++levels > 16) {
+            pc_set_error(ctx, "nested m-list: more than 16 levels");
+            rc = PC_EOVERFLOW;
+            break;
+        }
+        rc = buf_reserve(ctx, cnt, (lvn + 1) * 2 * sizeof(u32));
+        if (rc) break;
+        u32* c = cnt.as<u32>();
+        u32* off = c + lvn + 1;
+        NestPrefix* cur = all.as<NestPrefix>() + lv0;
+        nest_children_kernel<<<(unsigned)((lvn + 255) / 256), 256, 0, ctx->stream>>>(cur, (u32)lvn, primes, T.pi(),
+                                                                                     Y, c);
+        rc = scan_exclusive_u32_to_u32(ctx, c, off, lvn);
+        u32 nn = 0;
+        if (rc == PC_OK) rc = copy_to_host(ctx, &nn, off + lvn, sizeof(u32));
+        if (rc || nn == 0) break;
+        if (n_all + nn > cap) {
+            // grow the prefix array (the current level is copied along)
+            u64 ncap = cap;
+            while (n_all + nn > ncap) ncap *= 2;
+            rc = buf_reserve(ctx, nxt, ncap * sizeof(NestPrefix));
+            if (rc == PC_OK && cudaMemcpyAsync(nxt.p, all.p, n_all * sizeof(NestPrefix), cudaMemcpyDeviceToDevice,
+                                               ctx->stream) != cudaSuccess)
+                rc = PC_ECUDA;
+            if (rc) break;
+            std::swap(all, nxt);
+            buf_free(nxt);
+            cap = ncap;
+            cur = all.as<NestPrefix>() + lv0;
+        }
+        nest_expand_kernel<<<(unsigned)((lvn + 255) / 256), 256, 0, ctx->stream>>>(cur, (u32)lvn, off, primes,
+                                                                                   all.as<NestPrefix>() + n_all);
+        ctx->stats.kernel_launches += 2;
+        lv0 = n_all;
+        lvn = nn;
+        n_all += nn;
+    }
+    // entries per prefix, their offsets, then the rank bitset and the list
+    u64 nrw = Y / 64 + 1, total = 0;
+    if (rc == PC_OK) rc = buf_reserve(ctx, cnt, (n_all + 1) * sizeof(u32) + (n_all + 1) * sizeof(u64) + 8);
+    u32* ec = cnt.as<u32>();
+    u64* eoff = (u64*)(((uintptr_t)(ec + n_all + 1) + 7) & ~(uintptr_t)7);
+    if (rc == PC_OK) {
+        nest_entries_kernel<<<(unsigned)((n_all + 255) / 256), 256, 0, ctx->stream>>>(all.as<NestPrefix>(), n_all,
+                                                                                      T.pi(), Y, ec);
+        rc = scan_exclusive_u32_to_u64(ctx, ec, eoff, n_all);
+    }
+    if (rc == PC_OK) rc = copy_to_host(ctx, &total, eoff + n_all, sizeof(u64));
+    if (rc == PC_OK && total > 0xFFFFFFFFull) {
+        pc_set_error(ctx, "nested m-list: %llu entries", (unsigned long long)total);
+        rc = PC_EOVERFLOW;
+    }
+    if (rc == PC_OK) rc = buf_reserve(ctx, T.rank_bits, nrw * sizeof(u64));
+    if (rc == PC_OK) rc = buf_reserve(ctx, T.rank_cnt, (nrw + 1) * sizeof(u32));
+    if (rc == PC_OK && cudaMemsetAsync(T.rank_bits.p, 0, nrw * sizeof(u64), ctx->stream) != cudaSuccess) rc = PC_ECUDA;
+    const unsigned eg = (unsigned)((total + 255) / 256);
+    if (rc == PC_OK && total)
+        nest_mark_kernel<<<eg, 256, 0, ctx->stream>>>(all.as<NestPrefix>(), n_all, eoff, primes,
+                                                      T.rank_bits.as<u64>());
+    DevBuf tmp;
+    if (rc == PC_OK) rc = buf_reserve(ctx, tmp, (nrw + 1) * sizeof(u32));
+    if (rc == PC_OK) {
+        popc_words_kernel<<<(unsigned)((nrw + 255) / 256), 256, 0, ctx->stream>>>(T.rank_bits.as<u64>(), nrw,
+                                                                                 tmp.as<u32>());
+        rc = scan_exclusive_u32_to_u32(ctx, tmp.as<u32>(), T.rank_cnt.as<u32>(), nrw);
+    }
+    u32 members = 0;
+    if (rc == PC_OK) rc = copy_to_host(ctx, &members, T.rank_cnt.as<u32>() + nrw, sizeof(u32));
+    if (rc == PC_OK && members != total) {
+        // two entries with the same m would mean a product enumerated twice
+        pc_set_error(ctx, "nested m-list: %llu entries but %u distinct m", (unsigned long long)total, members);
+        rc = PC_EOVERFLOW;
+    }
+    if (rc == PC_OK) rc = buf_reserve(ctx, T.ml_m, (total + 1) * sizeof(u32));
+    if (rc == PC_OK) rc = buf_reserve(ctx, T.ml_info, (total + 1) * sizeof(u32));
+    if (rc == PC_OK) rc = buf_reserve(ctx, T.ml_gpf, (total + 1) * sizeof(u32));
+    if (rc == PC_OK) rc = buf_reserve(ctx, T.ml_rcp, (total + 1) * sizeof(u64));
+    if (rc == PC_OK && total) {
+        nest_scatter_kernel<<<eg, 256, 0, ctx->stream>>>(all.as<NestPrefix>(), n_all, eoff, primes,
+                                                         T.rank_bits.as<u64>(), T.rank_cnt.as<u32>(),
+                                                         T.ml_m.as<u32>(), T.ml_info.as<u32>(), T.ml_gpf.as<u32>());
+        reciprocal_kernel<<<eg, 256, 0, ctx->stream>>>(T.ml_m.as<u32>(), total, T.ml_rcp.as<u64>());
+        ctx->stats.kernel_launches += 3;
+    }
+    if (rc == PC_OK) {
+        const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            pc_set_error(ctx, "nested m-list build: %s", cudaGetErrorString(e));
+            rc = PC_ECUDA;
+        }
+    }
+    buf_free(tmp);
+    buf_free(cnt);
+    buf_free(all);
+    ctx->stats.kernel_launches += 2;
+    if (rc == PC_OK) {
+        T.ml_limit = Y;
+        T.ml_cmin = cmin;
+        T.ml_n = total;
+    }
+    return rc;
+}
+
 static int build_mlist(pc_ctx* ctx, u64 Y, u32 cmin)
 {
     Tables& T = ctx->T;
@@ -616,7 +843,7 @@ int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 
         if (lim < ml_limit) lim = ml_limit;
         u32 cm = cmin < T.ml_cmin ? cmin : T.ml_cmin;
         if (T.ml_limit == 0) cm = cmin;
-        PC_TRY(build_mlist(ctx, lim, cm));
+        PC_TRY(ctx->params.m_source == 1 ? build_mlist_nested(ctx, lim, cm) : build_mlist(ctx, lim, cm));
         PC_TRY(build_sublists(ctx));
     }
     // the odd-number pi table serves the easy leaves, whose u stays below the m-list limit y

@@ -260,6 +260,27 @@ def test_sampled_pi_table_parity(x, alpha):
                 assert got[k] == want[k], (x, y, c, k, got[k], want[k])
 
 
+@pytest.mark.parametrize("x,alpha", [(10 ** 9, 5), (10 ** 11, 2), (10 ** 12, 6), (2 ** 35, 3), (10 ** 10, 40)])
+def test_nested_mlist_parity(x, alpha):
+    # the m-list built by the nested loops of Section 2.2 (products of distinct primes,
+    # mu = (-1)^n) instead of the sieve of least prime factors: every leaf sum as the oracle's
+    y = y_for(x, alpha)
+    with pc.Context(0, m_source=1) as cx:
+        for c in (0, 3, 5, 7):
+            want = o.leaf_sums(x, y, c)
+            got = cx.leaf_sums(x, y, c)
+            for k in ("S1", "S2_triv", "S2_easy", "S2_hard", "P2"):
+                assert got[k] == want[k], (x, y, c, k, got[k], want[k])
+
+
+def test_nested_mlist_full_size(pi_pow10):
+    with pc.Context(0, m_source=1) as cx:
+        assert cx.pi_count(10 ** 16) == pi_pow10[16]
+        assert cx.pi_count(10 ** 18) == pi_pow10[18]
+        xs = [10 ** 9 + 7, 10 ** 11 + 1, 10 ** 15 + 3]
+        assert cx.pi_count_batch(xs) == [o.pi_meissel(x) if x <= 10 ** 11 + 1 else cx.pi_count(x) for x in xs]
+
+
 def test_sampled_pi_table_full_size(pi_pow10):
     with pc.Context(0, pi_gather=1) as cx:
         assert cx.pi_count(10 ** 16) == pi_pow10[16]
