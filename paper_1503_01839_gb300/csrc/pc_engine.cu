@@ -86,7 +86,7 @@ extern "C" void pc_destroy(pc_ctx* ctx)
     if (!ctx->borrowed) {
         Tables& T = ctx->T;
         DevBuf* tabs[] = {&T.small_primes, &T.pi_rec, &T.primes, &T.primes_rcp, &T.ml_m, &T.ml_info,
-                          &T.ml_gpf, &T.ml_rcp, &T.rank_bits, &T.rank_cnt, &T.samp, &T.primes_dv, &T.pi_odd};
+                          &T.ml_gpf, &T.ml_rcp, &T.rank_bits, &T.rank_cnt, &T.samp, &T.primes_dv, &T.pi_odd, &T.wheel19};
         for (DevBuf* b : tabs) buf_free(*b);
         for (int c = 0; c < 8; c++) buf_free(T.phiT[c]);
         for (int k = 0; k < Tables::NSUB; k++) {

@@ -75,6 +75,9 @@ struct Tables {
     DevBuf samp;
     u32 samp_s = 0;
     u64 samp_limit = 0;
+    // presieve pattern of the primes 7, 11, 13, 17, 19 (WHEEL19_PERIOD bytes of the mod-30
+    // bitset, then a copy of its start so that any 128 KiB slice is contiguous)
+    DevBuf wheel19;
     // odd-number pi table over [0, podd_limit] (pi_odd): one uint2 per 64 integers
     DevBuf pi_odd;
     u64 podd_limit = 0;
@@ -159,6 +162,10 @@ int copy_to_host(pc_ctx* ctx, void* dst, const void* src, size_t bytes);  // syn
 // prime_limit (plus one sentinel prime), and the m-list up to ml_limit with
 // lpf(m) > p_cmin.
 int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 cmin);
+// the presieve pattern of the primes 7..19 (Tables::wheel19), built once by a context that
+// owns its tables (tables_ensure does); a no-op for one that borrows them
+static constexpr u32 WHEEL19_PERIOD = 7u * 11u * 13u * 17u * 19u;   // bytes (30 integers each)
+int tables_wheel19(pc_ctx* ctx);
 int tables_phi_c(pc_ctx* ctx, u32 c);   // phi(., c) residue table
 // values of pi(v) for a handful of v (v <= pi_limit), synchronizing
 int tables_pi_values(pc_ctx* ctx, const u64* v, u64* out, int n);

@@ -27,6 +27,7 @@ struct P2Args {
     I128Pair* acc;    // sum of local counts per segment
     u32* queue;
     unsigned long long* stat;   // [3]: multiples crossed off (or null)
+    const u32* pat;   // presieve pattern of the primes 7..19 (k0 = 8), or null (7 and 11 from patw)
 };
 
 // Primes below P2_COOP_P have many wheel rounds per segment and are crossed
@@ -96,7 +97,8 @@ __global__ void __launch_bounds__(NT, 3) p2_sieve_kernel(P2Args A0, P2Multi M)
         }
         const P2Args& A = MULTI ? *(const P2Args*)sA_raw : A0;
         const u64 L = s * A.span;
-        fill_pattern(bits, seg_words, L, patw, A.k0);
+        if (A.pat) fill_pattern_global(bits, seg_words, L, A.pat, WHEEL19_PERIOD);
+        else fill_pattern(bits, seg_words, L, patw, A.k0);
         u32 ncl = 0;
         __syncthreads();
         const u64 end = L + A.span;
@@ -295,7 +297,14 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     A.z = z;
     A.r = r;
     A.B = (u32)B;
+    // 7..19 from the presieve pattern when they are all sieving primes (k0 = 8),
+    // else 7 and 11 from the small pattern
     A.k0 = B >= 5 ? 5 : (u32)B;
+    A.pat = nullptr;
+    if (B >= 8 && ctx->T.wheel19.bytes) {
+        A.k0 = 8;
+        A.pat = ctx->T.wheel19.as<u32>();
+    }
     // 32 KiB segments up to z = 2^30, 64 KiB beyond (measured on GB300: the small
     // segments win by a third at z ~ 1e8 and lose a few percent at z ~ 1.5e9)
 #ifndef PC_P2_BIG

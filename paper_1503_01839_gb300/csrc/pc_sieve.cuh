@@ -154,6 +154,17 @@ __device__ __forceinline__ void fill_pattern(u32* bits, u32 seg_words, u64 L, co
     }
 }
 
+// Fill from a pattern in global memory whose bytes repeat every `period` bytes and
+// which runs at least seg_words + 1 words past any phase: the segment's bytes are one
+// contiguous slice, read as aligned words and shifted by the phase's byte offset.
+__device__ __forceinline__ void fill_pattern_global(u32* bits, u32 seg_words, u64 L, const u32* pat, u32 period)
+{
+    const u32 o = (u32)((L / 30) % period);
+    const u32* src = pat + (o >> 2);
+    const u32 sh = 8 * (o & 3);
+    for (u32 w = threadIdx.x; w < seg_words; w += blockDim.x) bits[w] = __funnelshift_r(src[w], src[w + 1], sh);
+}
+
 // patw[ph] = 4 consecutive pattern bytes starting at phase ph (mod period)
 __device__ __forceinline__ void make_pattern_words(u32* patw, int depth)
 {

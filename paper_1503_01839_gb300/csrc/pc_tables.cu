@@ -396,6 +396,40 @@ static int build_primes(pc_ctx* ctx, u64 prime_limit)
     return PC_OK;
 }
 
+// ------------------------------------------- presieve pattern of 7..19
+// Byte g holds the integers 30 g + R8[j]; bit j is cleared when one of 7, 11, 13,
+// 17, 19 divides it (the primes themselves included).  The pattern repeats every
+// 7 * 11 * 13 * 17 * 19 bytes; the array runs 128 KiB + 8 bytes past one period, so
+// that a segment's words are one contiguous slice read at any phase.
+__global__ void wheel19_kernel(u32* words, u32 nwords)
+{
+    const u32 w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwords) return;
+    u32 v = 0;
+    for (u32 i = 0; i < 4; i++) {
+        const u32 g = (4 * w + i) % WHEEL19_PERIOD;
+        u32 byte = 0xFFu;
+        for (u32 j = 0; j < 8; j++) {
+            const u32 n = 30 * g + r8(j);   // < 2^24: no overflow
+            if (n % 7 == 0 || n % 11 == 0 || n % 13 == 0 || n % 17 == 0 || n % 19 == 0) byte &= ~(1u << j);
+        }
+        v |= byte << (8 * i);
+    }
+    words[w] = v;
+}
+
+int tables_wheel19(pc_ctx* ctx)
+{
+    Tables& T = ctx->T;
+    const u32 nwords = (WHEEL19_PERIOD + 131072 + 8 + 3) / 4;
+    if (T.wheel19.bytes >= nwords * sizeof(u32) || ctx->borrowed) return PC_OK;
+    PC_TRY(buf_reserve(ctx, T.wheel19, nwords * sizeof(u32)));
+    wheel19_kernel<<<(nwords + 255) / 256, 256, 0, ctx->stream>>>(T.wheel19.as<u32>(), nwords);
+    PC_LAUNCHED(ctx);
+    ctx->stats.kernel_launches++;
+    return PC_OK;
+}
+
 // ------------------------------------------------------ sampled pi table
 __global__ void sampled_kernel(PiTable pit, u64 n, u32 step, u32* samp)
 {
@@ -813,6 +847,7 @@ int tables_ensure(pc_ctx* ctx, u64 pi_limit, u64 prime_limit, u64 ml_limit, u32 
         return PC_EINVAL;
     }
     PC_TRY(ensure_small(ctx));
+    PC_TRY(tables_wheel19(ctx));
     bool new_pi = false;
     // The table is sieved with the bootstrap primes <= 65536, which suffice up to
     // 65536^2 = 2^32 (every query x < 2^63 needs at most isqrt(x) < 3.04e9).
