@@ -36,6 +36,50 @@ struct P2Args {
 // per prime.
 static constexpr u32 P2_COOP_P = 512;
 
+// The crossing walks of pc_sieve.cuh with 32-bit offsets, for p < 2^29: a byte offset
+// below 2^17 plus p, or an integer offset below 30 * 2^17 plus 6 p, stays below 2^32.
+// (P2's primes are at most isqrt(z) < 2^21 whenever y >= iroot3(x).)
+#ifndef P2_NARROW
+#define P2_NARROW 1
+#endif
+__device__ __forceinline__ u32 p2_cross_class(u32* bits, u32 seg_bytes, u64 L, u32 p, u64 kstart, u32 j)
+{
+    const u32 rj = r8(j);
+    u64 q = kstart / 30;
+    if (30 * q + rj < kstart) q++;
+    const u32 pr = p * rj;
+    const u32 bit = idx30(pr % 30);
+    const u64 byte64 = (u64)p * q + pr / 30;
+    const u64 Lb = L / 30;
+    if (byte64 < Lb || byte64 - Lb >= seg_bytes) return 0;
+    u32 n = 0;
+    for (u32 by = (u32)(byte64 - Lb); by < seg_bytes; by += p, n++) {
+        const u32 pos = (by << 3) + bit;
+        atomicAnd(&bits[pos >> 5], ~(1u << (pos & 31)));
+    }
+    return n;
+}
+
+__device__ __forceinline__ u32 p2_cross_single(u32* bits, u32 seg_bytes, u64 L, u32 p, u64 kstart)
+{
+    const u64 k = coprime30_at_or_after(kstart);
+    const u64 n0 = (u64)p * k;
+    const u32 span = 30 * seg_bytes;
+    if (n0 - L >= span) return 0;
+    u32 r = (u32)(k % 30), rel = (u32)(n0 - L), cnt = 0;
+    while (rel < span) {
+        cnt++;
+        const u32 q30 = rel / 30;
+        const u32 pos = q30 * 8 + idx30(rel - 30 * q30);
+        atomicAnd(&bits[pos >> 5], ~(1u << (pos & 31)));
+        const u32 d = next30(r);
+        r += d;
+        if (r >= 30) r -= 30;
+        rel += p * d;
+    }
+    return cnt;
+}
+
 // A launch over the segments of many queries (the batched form): item g is segment
 // g - qpref[q] of query q, with arguments qargs[q] (all with the same segment geometry).
 struct P2Multi {
@@ -115,13 +159,15 @@ __global__ void __launch_bounds__(NT, 3) p2_sieve_kernel(P2Args A0, P2Multi M)
             const u64 p = A.primes[bb];
             u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[bb]) : 0;
             if (ks < p) ks = p;
-            ncl += cross_off_class(bits, A.seg_bytes, L, (u32)p, ks, task & 7, none);
+            ncl += P2_NARROW && p < (1u << 29) ? p2_cross_class(bits, A.seg_bytes, L, (u32)p, ks, task & 7)
+                             : cross_off_class(bits, A.seg_bytes, L, (u32)p, ks, task & 7, none);
         }
         for (u32 bb = A.b_big + tid; bb <= A.B; bb += NT) {
             const u64 p = A.primes[bb];
             u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[bb]) : 0;
             if (ks < p) ks = p;
-            ncl += cross_off_single(bits, A.seg_bytes, L, (u32)p, ks, none);
+            ncl += P2_NARROW && p < (1u << 29) ? p2_cross_single(bits, A.seg_bytes, L, (u32)p, ks)
+                             : cross_off_single(bits, A.seg_bytes, L, (u32)p, ks, none);
         }
         // the sieving primes themselves (only in the first segments)
         for (u32 bb = A.k0 + 1 + tid; bb <= A.B; bb += NT) {
