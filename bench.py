@@ -153,9 +153,10 @@ HARD_SMEM = {"crossing": 1.0, "leaf": 17.0}
 HARD_INT = {"crossing": 4.0, "step": 16.0, "leaf": 48.0}
 # Easy leaves: per leaf resolved alone one division by a 32-bit reciprocal (two 32x32-bit
 # products, a shift and a remainder test: 8), the odd-number pi record's index and bit (3),
-# its popcount and sum (3) and the leaf's term (2); per run of clustered leaves two such
-# lookups and two divisions (32).  P2: one shared-memory atomic per crossing.
-EASY_INT = {"leaf": 16.0, "run": 32.0}
+# its popcount and sum (3) and the leaf's term (2); per run of clustered leaves, taken by its
+# pi value l, the same: one division by p_l, one lookup, and the run's term from the
+# neighbouring l's lookup (16).  P2: one shared-memory atomic per crossing.
+EASY_INT = {"leaf": 16.0, "run": 16.0}
 P2_SMEM = {"crossing": 1.0}
 
 
@@ -216,7 +217,7 @@ def other_rooflines(sp, n_sm, f_mhz):
         t = roofline_term(work, sp["ms_easy_kernel"], 128.0 * n_sm * f, "G int32-ops/s")
         t.update({"bound": "alu", "kernel_ms": sp["ms_easy_kernel"], "easy_leaves": sp["easy_leaves"],
                   "easy_runs": sp["easy_runs"], "easy_run_leaves": sp["easy_run_leaves"],
-                  "per_unit": "16 per leaf resolved alone, 32 per run of clustered leaves"})
+                  "per_unit": "16 per leaf resolved alone, 16 per run of clustered leaves"})
         nc = ncu_summary("easy_kernel", ("pc_leaves.cu", "pc_common.cuh"))
         if nc:
             t["ncu"] = {k: nc[k] for k in ("workload", "alu_pipe", "issue_active", "l2_hit", "dram_gbs") if k in nc}

@@ -180,23 +180,35 @@ int run_trivial(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 // Clustered easy leaves: when m is a prime q and u = x/(p_b q) is well below
 // q, consecutive q share the same pi(u).  With l = pi(u), every prime q' >= q
 // with q' <= (x/p_b) / p_l has pi(x/(p_b q')) = l as well (u only falls as q'
-// grows, and stays >= p_l), so the whole run counts (run length) * (l - b + 2)
-// from two pi lookups and two quotients (p_l is read off the pi record of u).  Those leaves (q^2 >= CLUST_K * x/p_b,
-// i.e. u <= q / CLUST_K) are walked run by run, each thread over a contiguous
-// slice; the rest one leaf per thread.  Chunks go to warps one at a time.
+// grows, and stays >= p_l), so the whole run counts (run length) * (l - b + 2).
+// Those leaves (q^2 >= CLUST_K * x/p_b, i.e. u <= q / CLUST_K) are taken run by
+// run; the rest one leaf per thread.  With the odd-number pi table the runs are
+// taken by their value l, 31 consecutive l per warp pass: the run of l holds the
+// clustered q with (x/p_b)/p_(l+1) < q <= (x/p_b)/p_l, so its length is a
+// difference of two pi lookups that neighbouring lanes share, and p_l's record is
+// read with its neighbours'.  Otherwise each thread walks the runs of a contiguous
+// slice of q, one pi lookup and two quotients per run.  Chunks go to warps one at
+// a time.
 static constexpr u32 EASY_CHUNK = 4096;     // leaves per chunk of the rest (128 per lane)
-static constexpr u64 CLUST_K = 3;
+static constexpr u64 CLUST_K = 2;   // measured: 2 beats 1 and 3 by about 1 % at pi(10^18)
 
 struct EasyRange {
     u64 i0, i1;   // list indices [i0, i1) or prime indices (i0, i1] shifted to [i0+1, i1+1)
     u64 im;       // first index of the clustered part (src 1), else i1
     u32 src;      // 0: m-list, 1: primes
-    u32 pad;
+    u32 l0, l1;   // clustered part: pi(u) runs from l0 (largest q) to l1 (smallest q)
 };
+
+// Clustered chunks taken by pi value (clust_chunk = 0, the odd-table path): the
+// clustered leaves of p_b with pi(u) = l, for every l in [l0, l1], CLUST_L values a chunk.
+static constexpr u32 CLUST_L = 31 * 128;
 
 __host__ __device__ inline u64 easy_chunks(const EasyRange& r, u32 clust_chunk)
 {
-    return (r.im - r.i0 + EASY_CHUNK - 1) / EASY_CHUNK + (r.i1 - r.im + clust_chunk - 1) / clust_chunk;
+    const u64 nclust = r.i1 <= r.im ? 0
+                       : clust_chunk ? (r.i1 - r.im + clust_chunk - 1) / clust_chunk
+                                     : ((u64)r.l1 - r.l0 + CLUST_L) / CLUST_L;
+    return (r.im - r.i0 + EASY_CHUNK - 1) / EASY_CHUNK + nclust;
 }
 
 // The easy leaves of prime p_b for a query (x, y, a): list indices [i0, i1) of the
@@ -208,7 +220,7 @@ __device__ __forceinline__ EasyRange easy_range(const LeafArgs& A, u64 x, u64 y,
     const u64 T = pc_min(p * p, y);
     const u64 lo = pc_max(y / p, xp / T);
     const u64 hi = pc_min(y, xp / p);
-    EasyRange r{0, 0, 0, 0, 0};
+    EasyRange r{0, 0, 0, 0, 0, 0};
     if (hi > lo) {
         if (p * p > y) {
             // lpf(m) > p_b and m <= y < p_b^2: m is a prime q, p_b < q <= p_a
@@ -221,6 +233,11 @@ __device__ __forceinline__ EasyRange easy_range(const LeafArgs& A, u64 x, u64 y,
                 // clustered from the first prime q with q^2 >= CLUST_K * x/p_b
                 const u64 qc = xp > ~0ull / CLUST_K ? hi + 1 : pc_isqrt(CLUST_K * xp - 1) + 1;
                 r.im = qc > hi ? r.i1 : pc_min(pc_max(pi_lookup(A.pit, qc - 1) + 1, r.i0), r.i1);
+                if (r.im < r.i1) {
+                    // u = x/(p_b q) <= q/3 < y: pi at the smallest and the largest clustered q
+                    r.l0 = (u32)pi_lookup(A.pit, xp / A.primes[r.i1 - 1]);
+                    r.l1 = (u32)pi_lookup(A.pit, xp / A.primes[r.im]);
+                }
             }
         } else {
             r.i0 = rank_lookup(A.rk, lo);
@@ -266,68 +283,84 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
     const u64 p = A.primes[b];
     const u64 xp = div_rcp(x, p, A.primes_rcp[b]);
     if (c >= nsp) {
+        if (MODE == PI_ODD && cc == 0) {
+            // Clustered chunk by pi value.  With G(l) = the number of clustered q (prime
+            // indices [im, i1)) with q <= (x/p_b)/p_l, exactly G(l) - G(l + 1) of them have
+            // pi(x/(p_b q)) = l, each adding l - b + 2.  Lane k takes l = base + k; lanes 0..30
+            // take their G(l + 1) from the next lane, so a pass covers 31 values of l, and
+            // each G costs one division (p_l's record, read coalesced) and one pi lookup.
+            const u32 lbase = r.l0 + (u32)(c - nsp) * CLUST_L;
+            const u32 lend = (u32)pc_min((u64)r.l1, (u64)lbase + CLUST_L - 1);   // inclusive
+            const u32 im = (u32)r.im, nq = (u32)(r.i1 - r.im);
+            const u64 qlast = A.primes[r.i1 - 1];
+            for (u32 l0 = lbase; l0 <= lend; l0 += 31) {
+                const u32 l = l0 + lane;
+                u32 G = 0;
+                if (l <= lend + 1) {   // p_l's record exists: l <= l1 + 1 <= pi(y) + 1
+                    // (x/p_b)/p_l < 2.3 y < 2^31; below qlast <= y it is inside the pi table
+                    const u32 v = div_dv(xp, A.primes_dv[l]);
+                    if (v >= qlast) {
+                        G = nq;
+                    } else {
+                        const i32 k = (i32)pi_odd(A.podd, v) - (i32)im + 1;   // v >= q_im / 2 >= 2
+                        G = k <= 0 ? 0u : ((u32)k > nq ? nq : (u32)k);
+                    }
+                }
+                const u32 Gn = __shfl_down_sync(0xffffffffu, G, 1);
+                if (lane < 31 && l <= lend) {
+                    const u32 n = G - Gn;
+                    s += (i64)n * ((i64)l - (i64)b + 2);
+                    n_runs += n != 0;
+                    n_run_leaves += n;
+                }
+            }
+            return;
+        }
         // clustered chunk: each thread walks the runs of its slice of primes q
         const u64 per = cc / 32;
         const u64 start = r.im + (c - nsp) * cc + lane * per;
         const u64 end = pc_min(r.i1, start + per);
         if (start >= end) return;
         const u64 qlast = A.primes[end - 1];
-        if constexpr (MODE == PI_ODD) {
-            for (u32 i = (u32)start; i < (u32)end;) {
-                const u32 u = div_dv(xp, A.primes_dv[i]);
-                const u32 l = pi_odd(A.podd, u);   // u >= p_b >= 2
-                u32 n = 1;
-                if (i + 1 < (u32)end) {
-                    // the run: primes q' <= (x/p_b) / p_l; p_l and its reciprocal are record l
-                    const u32 bound = div_dv(xp, A.primes_dv[l]);
-                    n = bound >= qlast ? (u32)end - i : pi_odd(A.podd, bound) - i + 1;
-                }
-                s += (i64)n * ((i64)l - (i64)b + 2);
-                n_runs++;
-                n_run_leaves += n;
-                i += n;
+        for (u64 i = start; i < end;) {
+            const u64 u = div_rcp(xp, A.primes[i], A.primes_rcp[i]);
+            u64 l, pl = 0, w = 0, bits = 0;
+            u32 hb0 = 0;
+            if (MODE == PI_SAMPLED) {
+                l = pi_sampled(A, u, &pl);
+            } else {
+                // pi(u) from u's record (u >= p_b >= 13, so 2, 3 and 5 all count)
+                // u < y < 2^32: the record is u / 240, its bit from u / 30 and u % 30
+                const u32 u32v = (u32)u, q30 = u32v / 30;
+                w = q30 >> 3;
+                const u32 e = 8 * (q30 & 7) + cntle30(u32v - 30 * q30);
+                const uint4 rq = __ldg((const uint4*)(A.pit.rec + w));
+                // the bits of the primes <= u, at the top of the word (shifted by 64 - e)
+                bits = low_bits_top((u64)rq.x | ((u64)rq.y << 32), e);
+                l = 3 + rq.z + __popcll(bits);
+                hb0 = e - 1;
             }
-        } else {
-            for (u64 i = start; i < end;) {
-                const u64 u = div_rcp(xp, A.primes[i], A.primes_rcp[i]);
-                u64 l, pl = 0, w = 0, bits = 0;
-                u32 hb0 = 0;
-                if (MODE == PI_SAMPLED) {
-                    l = pi_sampled(A, u, &pl);
-                } else {
-                    // pi(u) from u's record (u >= p_b >= 13, so 2, 3 and 5 all count)
-                    // u < y < 2^32: the record is u / 240, its bit from u / 30 and u % 30
-                    const u32 u32v = (u32)u, q30 = u32v / 30;
-                    w = q30 >> 3;
-                    const u32 e = 8 * (q30 & 7) + cntle30(u32v - 30 * q30);
-                    const uint4 rq = __ldg((const uint4*)(A.pit.rec + w));
-                    // the bits of the primes <= u, at the top of the word (shifted by 64 - e)
-                    bits = low_bits_top((u64)rq.x | ((u64)rq.y << 32), e);
-                    l = 3 + rq.z + __popcll(bits);
-                    hb0 = e - 1;
-                }
-                u64 n = 1;
-                if (i + 1 < end) {
-                    if (MODE == PI_REC) {
-                        // p_l, the largest prime <= u, from the same record when it holds one
-                        if (bits) {
-                            const u32 hb = hb0 - __clzll((long long)bits);   // its bit in the record
-                            pl = 240 * w + 30 * (hb >> 3) + r8(hb & 7);
-                        } else {
-                            pl = A.primes[l];
-                        }
+            u64 n = 1;
+            if (i + 1 < end) {
+                if (MODE == PI_REC) {
+                    // p_l, the largest prime <= u, from the same record when it holds one
+                    if (bits) {
+                        const u32 hb = hb0 - __clzll((long long)bits);   // its bit in the record
+                        pl = 240 * w + 30 * (hb >> 3) + r8(hb & 7);
+                    } else {
+                        pl = A.primes[l];
                     }
-                    // the run: primes q' <= (x/p_b) / p_l, by the reciprocal of p_l (its index is l)
-                    const u64 bound = div_rcp(xp, pl, A.primes_rcp[l]);
-                    u64 pb;
-                    n = bound >= qlast ? end - i
-                                       : (MODE == PI_SAMPLED ? pi_sampled(A, bound, &pb) : pi_lookup(A.pit, bound)) - i + 1;
                 }
-                s += (i64)n * ((i64)l - (i64)b + 2);
-                n_runs++;
-                n_run_leaves += (u32)n;
-                i += n;
+                // the run: primes q' <= (x/p_b) / p_l, by the reciprocal of p_l (its index is l)
+                const u64 bound = div_rcp(xp, pl, A.primes_rcp[l]);
+                u64 pb;
+                n = bound >= qlast ? end - i
+                                   : (MODE == PI_SAMPLED ? pi_sampled(A, bound, &pb) : pi_lookup(A.pit, bound)) - i + 1;
             }
+            s += (i64)n * ((i64)l - (i64)b + 2);
+            n_runs++;
+            n_run_leaves += (u32)n;
+            i += n;
         }
         return;
     }
@@ -421,6 +454,8 @@ int run_easy(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     u64* choff = ctx->easy_chunk_off.as<u64>();
     u32* nch = (u32*)(choff + nb + 1);
     LeafArgs A = make_args(ctx, P, 0);
+    const bool odd = !A.sampled && P.y < PI_ODD_Y && ctx->T.podd_limit >= P.y;
+    if (odd) A.clust_chunk = 0;   // clustered chunks by pi value
     easy_ranges_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, ctx->stream>>>(A, b_lo, nb,
                                                                               ctx->easy_rng.as<EasyRange>(), nch);
     PC_LAUNCHED(ctx);
@@ -449,7 +484,7 @@ int run_easy(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
     if (A.sampled)
         easy_kernel<PI_SAMPLED><<<g, 256, 0, ctx->stream>>>(A, b_lo, rng, choff, cmap, nchunks, queue,
                                                             ctx->partials.as<I128Pair>(), ctx->dstat);
-    else if (P.y < PI_ODD_Y && ctx->T.podd_limit >= P.y)
+    else if (odd)
         easy_kernel<PI_ODD><<<g, 256, 0, ctx->stream>>>(A, b_lo, rng, choff, cmap, nchunks, queue,
                                                         ctx->partials.as<I128Pair>(), ctx->dstat);
     else
@@ -626,7 +661,7 @@ __global__ void mq_easy_ranges_kernel(LeafArgs T, const MQ* qs, const u64* pref,
     const MQ m = qs[q];
     const EasyRange r = easy_range(T, m.x, m.y, m.a, m.c + 1 + (g - pref[q]));
     rng[g] = r;
-    nch[g] = (u32)easy_chunks(r, clust_chunk_for(m.x));
+    nch[g] = (u32)easy_chunks(r, 0);   // clustered chunks by pi value (odd-table path)
 }
 
 // every chunk of every (query, b), handed out to warps one at a time
@@ -646,7 +681,7 @@ __global__ void mq_easy_kernel(LeafArgs T, const MQ* qs, const u64* pref, u32 Q,
         const EasyRange r = rng[g];
         i64 s = 0;
         u32 n1 = 0, nr = 0, nrl = 0;
-        easy_chunk<PI_ODD>(T, m.x, m.a, m.c + 1 + (g - pref[q]), r, ch - choff[g], clust_chunk_for(m.x), lane, s,
+        easy_chunk<PI_ODD>(T, m.x, m.a, m.c + 1 + (g - pref[q]), r, ch - choff[g], 0, lane, s,
                           n1, nr, nrl);
         s = warp_sum_i64(s);
         if (lane == 0 && s) mq_atomic_add_i128(parts + 5 * q + 2, (i128)s);
