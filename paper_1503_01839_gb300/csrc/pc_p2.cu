@@ -16,7 +16,8 @@ struct P2Args {
     u64 x, y, z, r;   // r = isqrt(x)
     u32 B, k0;
     u32 b_mid, b_big;   // first prime index >= P2_COOP_P, and with 8 p > seg_bytes
-    u64 nseg;
+    u64 nseg;         // segments sieved: s0 .. s0 + nseg - 1 (arrays below indexed from s0)
+    u64 s0;           // first segment sieved: those below isqrt(x) hold no x/p (x/p >= isqrt x)
     u32 seg_bytes;
     u64 span;
     PiTable pit;
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(NT, 3) p2_sieve_kernel(P2Args A0, P2Multi M)
             break;
         }
         const P2Args& A = MULTI ? *(const P2Args*)sA_raw : A0;
-        const u64 L = s * A.span;
+        const u64 L = (s + A.s0) * A.span;
         if (A.pat) fill_pattern_global(bits, seg_words, L, A.pat, WHEEL19_PERIOD);
         else fill_pattern(bits, seg_words, L, patw, A.k0);
         u32 ncl = 0;
@@ -265,7 +266,16 @@ __global__ void p2_combine_kernel(P2Args A, I128Pair* out)
     __shared__ u64 s_carry;
     __shared__ i128 red[32];
     const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NT = blockDim.x;
-    if (threadIdx.x == 0) s_carry = 0;
+    if (threadIdx.x == 0) {
+        // phi(L_s0 - 1, B) for the segments not sieved: L_s0 - 1 < isqrt(x) < p_(B+1)^2, so it is
+        // pi(L_s0 - 1) - B + 1 from the pi table, or 1 (the integer 1 alone) below p_B
+        u64 c = 0;
+        if (A.s0) {
+            const u64 v = A.s0 * A.span - 1;
+            c = v >= A.primes[A.B] ? pi_lookup(A.pit, v) - A.B + 1 : 1;
+        }
+        s_carry = c;
+    }
     __syncthreads();
     i128 dot = 0;
     for (u64 base = 0; base < A.nseg; base += NT) {
@@ -364,7 +374,8 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
         A.b_mid = (u32)pc_min(pc_max(pv2[0] + 1, (u64)A.k0 + 1), B + 1);
         A.b_big = (u32)pc_min(pc_max(pv2[1] + 1, (u64)A.b_mid), B + 1);
     }
-    A.nseg = z / A.span + 1;
+    A.s0 = r / A.span;                   // r <= z since y < r
+    A.nseg = z / A.span + 1 - A.s0;
     A.pit = ctx->T.pi();
     A.primes = ctx->T.primes.as<u32>();
     A.primes_rcp = ctx->T.primes_rcp.as<u64>();
