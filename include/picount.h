@@ -101,7 +101,9 @@ typedef struct pc_stats {
     double ms_easy_kernel;    /* the easy-leaf kernel alone (CUDA events) */
     double ms_p2_kernel;      /* the P2 sieve kernel alone (CUDA events) */
     uint64_t easy_leaves;     /* easy leaves resolved one at a time */
-    uint64_t easy_runs;       /* runs of clustered easy leaves (one pi lookup pair each) */
+    uint64_t easy_runs;       /* runs of clustered easy leaves: with the odd-number pi table, the
+                                 (b, pi value) pairs taken (one division and one pi lookup each,
+                                 empty runs included); otherwise the runs walked */
     uint64_t easy_run_leaves; /* easy leaves those runs cover */
     uint64_t p2_clears;       /* multiples crossed off by the P2 sieve */
     uint64_t presieve_steps;  /* hard-leaf sieve: steps that replicas of heavy segments cross

@@ -293,6 +293,10 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
             const u32 lend = (u32)pc_min((u64)r.l1, (u64)lbase + CLUST_L - 1);   // inclusive
             const u32 im = (u32)r.im, nq = (u32)(r.i1 - r.im);
             const u64 qlast = A.primes[r.i1 - 1];
+            // sum over the lane's l of n_l * l; the - (b - 2) n_l part is added per chunk, from
+            // sum n_l = G(lbase) - G(lend + 1) (the differences telescope)
+            u64 nl = 0;
+            u32 g_first = 0, g_last = 0;
             for (u32 l0 = lbase; l0 <= lend; l0 += 31) {
                 const u32 l = l0 + lane;
                 u32 G = 0;
@@ -307,12 +311,18 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
                     }
                 }
                 const u32 Gn = __shfl_down_sync(0xffffffffu, G, 1);
-                if (lane < 31 && l <= lend) {
-                    const u32 n = G - Gn;
-                    s += (i64)n * ((i64)l - (i64)b + 2);
-                    n_runs += n != 0;
-                    n_run_leaves += n;
-                }
+                if (lane < 31 && l <= lend) nl += (u64)(G - Gn) * l;
+                if (l0 == lbase && lane == 0) g_first = G;
+                if (l == lend + 1) g_last = G;
+            }
+            // G(lbase) sits in lane 0, G(lend + 1) in the lane that computed it
+            const u32 gsum = __reduce_add_sync(0xffffffffu, g_last);
+            const u32 leaves = __shfl_sync(0xffffffffu, g_first, 0) - gsum;
+            s += (i64)nl;
+            if (lane == 0) {
+                s -= (i64)leaves * ((i64)b - 2);
+                n_runs += lend - lbase + 1;   // pi values taken
+                n_run_leaves += leaves;
             }
             return;
         }
