@@ -981,34 +981,32 @@ __global__ void row_len_kernel(const u32* segB, u64 nseg, u64 s0, u64 s1, u32 k0
 }
 
 // Upper bound of the hard leaves of every segment (the lpf filter of the
-// m-list is not applied): one thread per (b, s) row entry.
-__global__ void hard_estimate_kernel(HardArgs A, u64 total, u32 nrows, unsigned long long* est)
+// m-list is not applied): a warp per segment s in [s0, s1), its lanes over the
+// segment's leaf primes b (kleaf < b <= min(B_s, a)), one store per segment.
+__global__ void hard_estimate_kernel(HardArgs A, unsigned long long* est)
 {
-    for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (u64)gridDim.x * blockDim.x) {
-        u32 lo = 0, hi = nrows;   // largest row with off[row] <= e
-        while (hi - lo > 1) {
-            u32 mid = (lo + hi) >> 1;
-            if (A.off[mid] <= e) lo = mid; else hi = mid;
-        }
-        const u64 b = A.k0 + lo;
-        if (b <= A.kleaf || b > A.a) continue;
-        const u64 s = A.s0 + (e - A.off[lo]);
-        const u64 L = s * A.span;
+    const u64 s = A.s0 + ((u64)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const u32 lane = threadIdx.x & 31;
+    if (s >= A.s1) return;   // the whole warp
+    const u64 L = s * A.span, vL = A.rcp_seg[2 * s], vLs = A.rcp_seg[2 * s + 1];
+    const u64 bhi = pc_min((u64)A.segB[s], A.a);
+    u64 n = 0;
+    for (u64 b = A.kleaf + 1 + lane; b <= bhi; b += 32) {
         const u64 p = A.primes[b];
         const u64 vp = A.primes_rcp[b];
         const u64 xp = div_rcp(A.x, p, vp);
         u64 mlo, mhi;
-        if (!leaf_window(A, p, vp, xp, L, A.rcp_seg[2 * s], A.rcp_seg[2 * s + 1], mlo, mhi)) continue;
-        u64 n;
+        if (!leaf_window(A, p, vp, xp, L, vL, vLs, mlo, mhi)) continue;
         if (p * p > A.y) {
             const u64 k0 = pc_min(pc_max(pi_lookup(A.pit, mlo), b), A.a);
             const u64 k1 = pc_min(pc_max(pi_lookup(A.pit, mhi), b), A.a);
-            n = k1 - k0;
+            n += k1 - k0;
         } else {
-            n = rank_lookup(A.rk, mhi) - rank_lookup(A.rk, mlo);
+            n += rank_lookup(A.rk, mhi) - rank_lookup(A.rk, mlo);
         }
-        if (n) atomicAdd(est + s, (unsigned long long)n);
     }
+    for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if (lane == 0) est[s] = n;
 }
 
 // S2_hard carries: for each leaf prime b, the exclusive scan over segments
@@ -1450,9 +1448,11 @@ int run_hard_sieve(pc_ctx* ctx, const LeafProblem& P, I128Pair* out)
 
     // per-segment leaf estimate, then the work items, all on the device
     PC_CUDA(ctx, cudaMemsetAsync(est, 0, A.nseg * sizeof(u64), ctx->stream));
-    hard_estimate_kernel<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(A, total, (u32)nrows, est);
-    PC_LAUNCHED(ctx);
-    ctx->stats.kernel_launches++;
+    if (A.s1 > A.s0) {
+        hard_estimate_kernel<<<(unsigned)(((A.s1 - A.s0) * 32 + 255) / 256), 256, 0, ctx->stream>>>(A, est);
+        PC_LAUNCHED(ctx);
+        ctx->stats.kernel_launches++;
+    }
     const u64 cap = (A.s1 - A.s0) + 8ull * (u64)ctas + 64;
     const size_t items_bytes = (size_t)ctas * sizeof(I128Pair) + cap * sizeof(HardItem);
     PC_TRY(buf_reserve(ctx, ctx->counts, total * sizeof(u32)));

@@ -103,6 +103,19 @@ def test_p2_parity(ctx_small, ctx):
         assert ctx.p2(x, y) == want
 
 
+def test_p2_first_sieved_segment(ctx, ctx_small):
+    # P2 sieves from the segment that holds isqrt(x), its starting count phi(L - 1, B) taken
+    # from the pi table: x at and around squares of the segment span (30 * 32768 bytes for
+    # the default context below z = 2^30, 30 * 1024 for the small one)
+    for cx, span in ((ctx, 30 * 32768), (ctx_small, 30 * 1024)):
+        for k, d in ((1, -1), (1, 0), (1, 1), (2, 0), (3, 7)):
+            x = (k * span) ** 2 + d
+            y = max(20000, o.iroot3(x) + 1)   # the domain of pc_p2: iroot3(x) <= y <= isqrt(x)
+            if y > math.isqrt(x):
+                continue
+            assert cx.p2(x, y) == o.p2(x, o.pi_sieve(y)), (x, y, span)
+
+
 def test_pi_count_table1(ctx, pi_pow10):
     for n in range(1, 19):
         assert ctx.pi_count(10 ** n) == pi_pow10[n], n
