@@ -22,6 +22,11 @@ struct LeafArgs {
     PiTable pit;
     RankTable rk;
     MList ml;
+    // sub-lists of the m-list (lpf index > slK[k]); the easy leaves of p_b are read from
+    // the last one with slK <= b, else from ml
+    MList sl[Tables::NSUB];
+    RankTable srk[Tables::NSUB];
+    u32 slK[Tables::NSUB];
     const u32* primes;
     const u64* primes_rcp;   // floor((2^64 - 1) / p_k)
     const u64* primes_dv;    // p_k and its 32-bit reciprocal (div_dv)
@@ -64,6 +69,11 @@ static LeafArgs make_args(pc_ctx* ctx, const LeafProblem& P, u64 n_lim)
     A.pit = ctx->T.pi();
     A.rk = ctx->T.rank();
     A.ml = ctx->T.mlist();
+    for (int k = 0; k < Tables::NSUB; k++) {
+        A.sl[k] = ctx->T.sublist(k);
+        A.srk[k] = ctx->T.subrank(k);
+        A.slK[k] = k < (int)ctx->T.n_sl ? ctx->T.sl_K[k] : ~0u;
+    }
     A.primes = ctx->T.primes.as<u32>();
     A.primes_rcp = ctx->T.primes_rcp.as<u64>();
     A.primes_dv = ctx->T.primes_dv.as<u64>();
@@ -197,6 +207,7 @@ struct EasyRange {
     u64 im;       // first index of the clustered part (src 1), else i1
     u32 src;      // 0: m-list, 1: primes
     u32 l0, l1;   // clustered part: pi(u) runs from l0 (largest q) to l1 (smallest q)
+    u32 ls;       // src 0: the list read, 0 for the m-list, k + 1 for its sub-list k
 };
 
 // Clustered chunks taken by pi value (clust_chunk = 0, the odd-table path): the
@@ -220,7 +231,7 @@ __device__ __forceinline__ EasyRange easy_range(const LeafArgs& A, u64 x, u64 y,
     const u64 T = pc_min(p * p, y);
     const u64 lo = pc_max(y / p, xp / T);
     const u64 hi = pc_min(y, xp / p);
-    EasyRange r{0, 0, 0, 0, 0, 0};
+    EasyRange r{0, 0, 0, 0, 0, 0, 0};
     if (hi > lo) {
         if (p * p > y) {
             // lpf(m) > p_b and m <= y < p_b^2: m is a prime q, p_b < q <= p_a
@@ -240,9 +251,16 @@ __device__ __forceinline__ EasyRange easy_range(const LeafArgs& A, u64 x, u64 y,
                 }
             }
         } else {
-            r.i0 = rank_lookup(A.rk, lo);
-            r.i1 = rank_lookup(A.rk, hi);
+            // the last sub-list whose entries all have lpf index > K, K <= b: it holds every
+            // leaf of p_b and fewer entries to skip (lpf <= p_b) than the whole m-list
+            u32 li = 0;
+            for (int k = 0; k < Tables::NSUB; k++)
+                if (A.slK[k] <= b) li = k + 1;
+            const RankTable& R = li ? A.srk[li - 1] : A.rk;
+            r.i0 = rank_lookup(R, lo);
+            r.i1 = rank_lookup(R, hi);
             r.src = 0;
+            r.ls = li;
         }
     }
     if (r.src == 0) r.im = r.i1;
@@ -392,11 +410,12 @@ __device__ __forceinline__ void easy_chunk(const LeafArgs& A, u64 x, u64 a, u64 
             m = A.primes[i];
             v = A.primes_rcp[i];
         } else {
-            const u32 info = A.ml.info[i];
+            const MList& ml = r.ls ? A.sl[r.ls - 1] : A.ml;
+            const u32 info = ml.info[i];
             if ((info >> 1) <= b) continue;
-            if (A.trunc && A.ml.gpf[i] > a) continue;
-            m = A.ml.m[i];
-            v = A.ml.rcp[i];
+            if (A.trunc && ml.gpf[i] > a) continue;
+            m = ml.m[i];
+            v = ml.rcp[i];
             neg = info & 1;
         }
         // easy: p_b <= u < y < 2^32; for b > 3, u >= 7 and pi(u) counts 2, 3, 5
