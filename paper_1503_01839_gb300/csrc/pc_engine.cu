@@ -201,8 +201,9 @@ u32 default_alpha(u64 x)
     if (d <= 13) return 16;
     if (d == 14) return 24;
     if (d == 15) return 20;
-    if (d <= 17) return 32;
-    return 40;
+    if (d == 16) return 32;
+    if (d == 17) return 40;
+    return 56;
 }
 
 int decimal_digits(u64 x)
