@@ -361,12 +361,10 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
         A.k0 = 8;
         A.pat = ctx->T.wheel19.as<u32>();
     }
-    // 32 KiB segments up to z = 2^30, 64 KiB beyond (measured on GB300: the small
-    // segments win by a third at z ~ 1e8 and lose a few percent at z ~ 1.5e9)
-#ifndef PC_P2_BIG
-#define PC_P2_BIG 65536
-#endif
-    A.seg_bytes = pc_seg_bytes(ctx, A.z < (1ull << 30) ? 32768 : PC_P2_BIG);
+    // 32 KiB segments up to z = 2^30, 64 KiB up to 2^32, 48 KiB beyond (measured on
+    // GB300: the small segments win by a third at z ~ 1e8 and lose a few percent at
+    // z ~ 1.5e9; 48 KiB against 64 KiB: pi(1e17) P2 2.45 -> 2.38 ms, pi(1e18) 8.9 -> 8.5 ms)
+    A.seg_bytes = pc_seg_bytes(ctx, A.z < (1ull << 30) ? 32768 : A.z < (1ull << 32) ? 65536 : 49152);
     A.span = 30ull * A.seg_bytes;
     {
         u64 v2[2] = {P2_COOP_P - 1, A.seg_bytes / 8}, pv2[2];
@@ -470,6 +468,7 @@ __global__ void mq_final_kernel(const MQ* qs, u32 Q, const I128Pair* parts, u64*
 
 int mq_final(pc_ctx* ctx, const MQPlan& P, u64* d_out, int* d_bad)
 {
+    if (!mq_device_work(ctx)) return PC_OK;
     mq_final_kernel<<<(P.Q + 127) / 128, 128, 0, ctx->stream>>>(P.dq, P.Q, P.parts, d_out, d_bad);
     PC_LAUNCHED(ctx);
     ctx->stats.kernel_launches++;
@@ -487,7 +486,14 @@ int mq_p2(pc_ctx* ctx, const MQPlan& P)
     T.primes = ctx->T.primes.as<u32>();
     T.primes_rcp = ctx->T.primes_rcp.as<u64>();
     u64 v2[2] = {P2_COOP_P - 1, T.seg_bytes / 8}, pv2[2];
-    PC_TRY(tables_pi_values(ctx, v2, pv2, 2));
+    if (ctx->mq_mode == MQ_CAPTURE) {   // a read-back: taken in the prepare pass
+        pv2[0] = ctx->mq_p2_pv[0];
+        pv2[1] = ctx->mq_p2_pv[1];
+    } else {
+        PC_TRY(tables_pi_values(ctx, v2, pv2, 2));
+        ctx->mq_p2_pv[0] = pv2[0];
+        ctx->mq_p2_pv[1] = pv2[1];
+    }
     std::vector<u64> spref(Q + 1, 0);
     for (u32 q = 0; q < Q; q++) {
         const MQ& m = P.hq[q];
@@ -534,18 +540,23 @@ int mq_p2(pc_ctx* ctx, const MQPlan& P)
         A.stat = nullptr;
     }
     cudaStream_t st = ctx->stream;
-    PC_CUDA(ctx, cudaMemcpyAsync(d_qa, qa.data(), Q * sizeof(P2Args), cudaMemcpyHostToDevice, st));
-    PC_CUDA(ctx, cudaMemcpyAsync(d_ipref, ipref.data(), (Q + 1) * 4, cudaMemcpyHostToDevice, st));
-    PC_CUDA(ctx, cudaMemsetAsync(d_queue, 0, 64, st));
-    if (S) {
-        const u32 nblk = T.seg_bytes >> 7;
-        const size_t smem = T.seg_bytes + (2 * (size_t)nblk + 2) * sizeof(u32);
+    if (mq_host_upload(ctx)) {
+        PC_CUDA(ctx, cudaMemcpyAsync(d_qa, qa.data(), Q * sizeof(P2Args), cudaMemcpyHostToDevice, st));
+        PC_CUDA(ctx, cudaMemcpyAsync(d_ipref, ipref.data(), (Q + 1) * 4, cudaMemcpyHostToDevice, st));
+    }
+    const u32 nblk = T.seg_bytes >> 7;
+    const size_t smem = T.seg_bytes + (2 * (size_t)nblk + 2) * sizeof(u32);
+    if (S && ctx->mq_mode != MQ_CAPTURE) {   // the shared-memory limit, set outside any capture
         cudaFuncAttributes fa;
         PC_CUDA(ctx, cudaFuncGetAttributes(&fa, p2_sieve_kernel<512, true>));
         const size_t dyn_max = ctx->smem_optin - fa.sharedSizeBytes;
         if (smem > dyn_max) return PC_EINVAL;
         PC_CUDA(ctx, cudaFuncSetAttribute(p2_sieve_kernel<512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)dyn_max));
+    }
+    if (!mq_device_work(ctx)) return PC_OK;
+    PC_CUDA(ctx, cudaMemsetAsync(d_queue, 0, 64, st));
+    if (S) {
         int per_sm = (int)(ctx->smem_optin / (smem + 4096));
         if (per_sm < 1) per_sm = 1;
         if (per_sm > 4) per_sm = 4;
