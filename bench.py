@@ -388,7 +388,8 @@ def run_batch(local, n, streams, seed=0):
         t0 = time.perf_counter()
         got = cx.pi_count_batch(xs)
         tb = time.perf_counter() - t0
-        launches = cx.stats()["kernel_launches"]
+        bst = cx.stats()
+        launches = bst["kernel_launches"]
         t0 = time.perf_counter()
         plain = [cx.pi_count(v) for v in xs]
         tl = time.perf_counter() - t0
@@ -398,6 +399,7 @@ def run_batch(local, n, streams, seed=0):
     return {"queries": n, "x": "floor(10^e), e ~ U(8, 15), numpy default_rng(%d)" % seed, "x_sha256": sha,
             "slots": streams, "batch_s": tb, "batch_qps": n / tb, "plain_loop_s": tl, "plain_qps": n / tl,
             "speedup": tl / tb, "bit_exact": True, "gpu_launches": launches,
+            "graph_launches": bst["graph_launches"], "graph_nodes": bst["graph_nodes"],
             "autotune_s": t_tune, "tuned_alpha_seg_ctas_per_decade": tuned}
 
 

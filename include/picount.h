@@ -77,6 +77,10 @@ typedef struct pc_params {
                              1 = the nested loops of Section 2.2 over products of
                              distinct primes, mu = (-1)^(number of primes), with
                              no per-integer table.  Both give the same list. */
+    uint32_t batch_launch; /* how pc_pi_count_batch runs its one schedule: 0 = the
+                             device work of every phase captured into one CUDA
+                             graph and launched once (the default); 1 = the same
+                             kernels launched one by one */
 } pc_params;
 
 /* Counters and phase times of the last successful call. */
@@ -108,6 +112,9 @@ typedef struct pc_stats {
     uint64_t p2_clears;       /* multiples crossed off by the P2 sieve */
     uint64_t presieve_steps;  /* hard-leaf sieve: steps that replicas of heavy segments cross
                                  off, with no counts, before the steps they own */
+    uint64_t graph_launches;  /* pc_pi_count_batch: CUDA graphs launched (the schedule's
+                                 kernels, counted in kernel_launches, are its nodes) */
+    uint64_t graph_nodes;     /* nodes of that graph (kernels and memsets) */
 } pc_stats;
 
 typedef struct pc_ctx pc_ctx;

@@ -39,7 +39,8 @@ class PcI128(ctypes.Structure):
 class PcParams(ctypes.Structure):
     _fields_ = [("seg_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("threads", ctypes.c_uint32),
                 ("alpha", ctypes.c_uint32), ("c", ctypes.c_uint32), ("warp_bytes", ctypes.c_uint32),
-                ("streams", ctypes.c_uint32), ("pi_gather", ctypes.c_uint32), ("m_source", ctypes.c_uint32)]
+                ("streams", ctypes.c_uint32), ("pi_gather", ctypes.c_uint32), ("m_source", ctypes.c_uint32),
+                ("batch_launch", ctypes.c_uint32)]
 
 
 class PcStats(ctypes.Structure):
@@ -55,7 +56,8 @@ class PcStats(ctypes.Structure):
                 ("ms_easy_kernel", ctypes.c_double), ("ms_p2_kernel", ctypes.c_double),
                 ("easy_leaves", ctypes.c_uint64), ("easy_runs", ctypes.c_uint64),
                 ("easy_run_leaves", ctypes.c_uint64), ("p2_clears", ctypes.c_uint64),
-                ("presieve_steps", ctypes.c_uint64)]
+                ("presieve_steps", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
+                ("graph_nodes", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -144,9 +146,10 @@ class Context:
 
     def __init__(self, device: int = 0, seg_bytes: int = 0, ctas_per_sm: int = 0, threads: int = 0,
                  alpha: int = 0, c: int = 0, warp_bytes: int = 0, streams: int = 0, pi_gather: int = 0,
-                 m_source: int = 0):
+                 m_source: int = 0, batch_launch: int = 0):
         self._L = lib()
-        prm = PcParams(seg_bytes, ctas_per_sm, threads, alpha, c, warp_bytes, streams, pi_gather, m_source)
+        prm = PcParams(seg_bytes, ctas_per_sm, threads, alpha, c, warp_bytes, streams, pi_gather, m_source,
+                       batch_launch)
         h = ctypes.c_void_p()
         rc = self._L.pc_create(ctypes.byref(h), device, ctypes.byref(prm))
         if rc != PC_OK:

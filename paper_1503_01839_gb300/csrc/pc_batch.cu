@@ -225,6 +225,47 @@ int mq_final(pc_ctx* ctx, const MQPlan& P, u64* d_out, int* d_bad);
 // sorted largest first, so that the sieve launches start on the longest segments.
 static constexpr u64 MQ_MAX = 10000000000000000ull;   // 1e16: larger ones run one by one
 
+// every phase after the read-back of mq_info, in the context's mode (ctx->mq_mode)
+static int mq_phases(pc_ctx* ctx, const MQPlan& P, u64* d_out, int* d_bad)
+{
+    PC_TRY(mq_s1_trivial(ctx, P));
+    PC_TRY(mq_easy(ctx, P));
+    PC_TRY(mq_hard(ctx, P));
+    PC_TRY(mq_p2(ctx, P));
+    return mq_final(ctx, P, d_out, d_bad);
+}
+
+// The phases' device work (kernels and memsets, no host copies: the prepare pass made
+// those), captured from the context's stream into one executable graph.  The capture
+// is always ended, so the stream leaves capture mode on every path.
+static int mq_capture(pc_ctx* ctx, const MQPlan& P, u64* d_out, int* d_bad, cudaGraphExec_t* out)
+{
+    PC_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ctx->mq_mode = MQ_CAPTURE;
+    const int rc = mq_phases(ctx, P, d_out, d_bad);
+    ctx->mq_mode = MQ_DIRECT;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g);
+    if (rc != PC_OK || ec != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (rc != PC_OK) return rc;
+        pc_set_error(ctx, "batch graph capture: %s", cudaGetErrorString(ec));
+        return PC_ECUDA;
+    }
+    size_t nodes = 0;
+    cudaGraphGetNodes(g, nullptr, &nodes);
+    const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        pc_set_error(ctx, "batch graph instantiate: %s", cudaGetErrorString(ei));
+        return PC_ECUDA;
+    }
+    ctx->stats.graph_nodes = nodes;
+    return PC_OK;
+}
+
 static int multi_batch(pc_ctx* ctx, const std::vector<u64>& xs, std::vector<u64>& out)
 {
     const u32 n = (u32)xs.size();
@@ -261,16 +302,35 @@ static int multi_batch(pc_ctx* ctx, const std::vector<u64>& xs, std::vector<u64>
     PC_CUDA(ctx, cudaMemcpyAsync(base, P.hq.data(), n * sizeof(MQ), cudaMemcpyHostToDevice, ctx->stream));
     PC_CUDA(ctx, cudaMemsetAsync(P.parts, 0, (size_t)n * 5 * sizeof(I128Pair) + (size_t)n * 8 + 16, ctx->stream));
     PC_TRY(mq_info(ctx, P));   // the batch's one read-back before the leaf sums
-    PC_TRY(mq_s1_trivial(ctx, P));
-    PC_TRY(mq_easy(ctx, P));
-    PC_TRY(mq_hard(ctx, P));
-    PC_TRY(mq_p2(ctx, P));
-    PC_TRY(mq_final(ctx, P, d_out, d_bad));
+    cudaGraphExec_t exec = nullptr;
+    if (ctx->params.batch_launch == 0) {
+        // prepare (scratch, uploads, table reads), then capture the device work of every
+        // phase into one graph and launch it
+        ctx->mq_mode = MQ_PREPARE;
+        const int rc = mq_phases(ctx, P, d_out, d_bad);
+        ctx->mq_mode = MQ_DIRECT;
+        PC_TRY(rc);
+        PC_TRY(mq_capture(ctx, P, d_out, d_bad, &exec));
+        const cudaError_t e = cudaGraphLaunch(exec, ctx->stream);
+        if (e != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            pc_set_error(ctx, "batch graph launch: %s", cudaGetErrorString(e));
+            return PC_ECUDA;
+        }
+        ctx->stats.graph_launches++;
+    } else {
+        PC_TRY(mq_phases(ctx, P, d_out, d_bad));
+    }
     std::vector<u64> res(n);
     int bad = 0;
-    PC_CUDA(ctx, cudaMemcpyAsync(res.data(), d_out, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    PC_CUDA(ctx, cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    PC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaError_t e1 = cudaMemcpyAsync(res.data(), d_out, n * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(ctx->stream);
+    if (exec) cudaGraphExecDestroy(exec);   // after the stream has drained
+    if (e1 != cudaSuccess) {
+        pc_set_error(ctx, "batch read-back: %s", cudaGetErrorString(e1));
+        return PC_ECUDA;
+    }
     if (bad) {
         pc_set_error(ctx, "batch: pi(x) out of range (internal inconsistency)");
         return PC_EOVERFLOW;
@@ -323,12 +383,14 @@ extern "C" int pc_pi_count_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint
         for (size_t k = 0; k < sx.size(); k++) hout[si[k]] = sv[k];
         ctx->stats.kernel_launches++;
     }
-    u64 launches = ctx->stats.kernel_launches;
+    u64 launches = ctx->stats.kernel_launches, glaunch = 0, gnodes = 0;
     if (!mx.empty()) {
         std::vector<u64> mv(mx.size());
         PC_TRY(multi_batch(ctx, mx, mv));
         for (size_t k = 0; k < mx.size(); k++) hout[mi[k]] = mv[k];
         launches = ctx->stats.kernel_launches;
+        glaunch = ctx->stats.graph_launches;
+        gnodes = ctx->stats.graph_nodes;
     }
     for (size_t k = 0; k < bx.size(); k++) {
         u64 v = 0;
@@ -339,6 +401,8 @@ extern "C" int pc_pi_count_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint
     }
     memset(&ctx->stats, 0, sizeof(ctx->stats));
     ctx->stats.kernel_launches = launches;
+    ctx->stats.graph_launches = glaunch;
+    ctx->stats.graph_nodes = gnodes;
     if (stream) {
         PC_CUDA(ctx, cudaMemcpyAsync(out, hout.data(), n * sizeof(u64), cudaMemcpyHostToDevice, (cudaStream_t)stream));
         PC_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));

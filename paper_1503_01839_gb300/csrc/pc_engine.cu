@@ -46,7 +46,7 @@ extern "C" int pc_create(pc_ctx** out, int device, const pc_params* p)
     const uint32_t wb = ctx->params.warp_bytes;
     if (ctx->params.c > 7 || (sb && sb != 1024 && sb != 2048 && (sb % 4096 || sb > 131072)) ||
         (wb && wb != 1024 && wb != 2048 && wb != 4096 && wb != 8192) ||
-        ctx->params.ctas_per_sm > 4 || ctx->params.pi_gather > 1 || ctx->params.m_source > 1 ||
+        ctx->params.ctas_per_sm > 4 || ctx->params.pi_gather > 1 || ctx->params.m_source > 1 || ctx->params.batch_launch > 1 ||
         (ctx->params.threads && (ctx->params.threads % 32 || ctx->params.threads < 128 || ctx->params.threads > 1024))) {
         delete ctx;
         return PC_EINVAL;

@@ -1688,11 +1688,25 @@ int mq_hard(pc_ctx* ctx, const MQPlan& P)
         A.stat = (unsigned long long*)(d_queue + 2);
     }
     cudaStream_t st = ctx->stream;
-    PC_CUDA(ctx, cudaMemcpyAsync(d_qa, qa.data(), Q * sizeof(HardArgs), cudaMemcpyHostToDevice, st));
-    PC_CUDA(ctx, cudaMemcpyAsync(d_spref, spref.data(), (Q + 1) * 8, cudaMemcpyHostToDevice, st));
-    PC_CUDA(ctx, cudaMemcpyAsync(d_rpref, rpref.data(), (Q + 1) * 8, cudaMemcpyHostToDevice, st));
-    PC_CUDA(ctx, cudaMemcpyAsync(d_cpref, cpref.data(), (Q + 1) * 8, cudaMemcpyHostToDevice, st));
-    PC_CUDA(ctx, cudaMemcpyAsync(d_ipref, ipref.data(), (Q + 1) * 4, cudaMemcpyHostToDevice, st));
+    if (mq_host_upload(ctx)) {
+        PC_CUDA(ctx, cudaMemcpyAsync(d_qa, qa.data(), Q * sizeof(HardArgs), cudaMemcpyHostToDevice, st));
+        PC_CUDA(ctx, cudaMemcpyAsync(d_spref, spref.data(), (Q + 1) * 8, cudaMemcpyHostToDevice, st));
+        PC_CUDA(ctx, cudaMemcpyAsync(d_rpref, rpref.data(), (Q + 1) * 8, cudaMemcpyHostToDevice, st));
+        PC_CUDA(ctx, cudaMemcpyAsync(d_cpref, cpref.data(), (Q + 1) * 8, cudaMemcpyHostToDevice, st));
+        PC_CUDA(ctx, cudaMemcpyAsync(d_ipref, ipref.data(), (Q + 1) * 4, cudaMemcpyHostToDevice, st));
+    }
+    // the sieve's instantiation (its shared-memory attribute set outside any capture)
+    T.queue = d_queue;
+    T.stat = (unsigned long long*)(d_queue + 2);
+    const size_t smem = hard_smem(T);
+    if (ctx->mq_mode != MQ_CAPTURE) {
+        void (*kern)(HardArgs, MultiArgs) = nullptr;
+        int per_sm = 0;
+        PC_TRY(choose_hard_kernel<true>(ctx, T, smem, &kern, &per_sm));
+        ctx->mq_hard_kern = (void*)kern;
+        ctx->mq_hard_per_sm = per_sm;
+    }
+    if (!mq_device_work(ctx)) return scan_exclusive_u32_to_u64(ctx, d_rowlen, d_off, R);   // its scratch only
     PC_CUDA(ctx, cudaMemsetAsync(d_queue, 0, 128, st));
     PC_CUDA(ctx, cudaMemsetAsync(ctx->tallies.p, 0, bound * sizeof(i32), st));
     mq_seg_b_kernel<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(d_qa, d_spref, Q, d_segB, d_rcp);
@@ -1701,12 +1715,8 @@ int mq_hard(pc_ctx* ctx, const MQPlan& P)
     PC_LAUNCHED(ctx);
     PC_TRY(scan_exclusive_u32_to_u64(ctx, d_rowlen, d_off, R));
     // the sieve: items are the segments of every query, handed out in order
-    T.queue = d_queue;
-    T.stat = (unsigned long long*)(d_queue + 2);
-    const size_t smem = hard_smem(T);
-    void (*kern)(HardArgs, MultiArgs) = nullptr;
-    int per_sm = 0;
-    PC_TRY(choose_hard_kernel<true>(ctx, T, smem, &kern, &per_sm));
+    void (*kern)(HardArgs, MultiArgs) = (void (*)(HardArgs, MultiArgs))ctx->mq_hard_kern;
+    const int per_sm = ctx->mq_hard_per_sm;
     const u64 ctas = pc_min((u64)ctx->sm_count * per_sm, S);
     MultiArgs M{d_qa, d_ipref, Q, (unsigned long long)S, P.parts + 3, 5u};
     kern<<<(unsigned)ctas, 32 * T.nw, smem, st>>>(T, M);

@@ -134,7 +134,19 @@ struct pc_ctx {
     // beside the result slots; null outside a leaf-sum call
     unsigned long long* dstat = nullptr;
     bool easy_timed = false, p2_timed = false;   // ev[2..3] / ev[4..5] hold kernel times
+    // How the batched phases (mq_*) run: MQ_DIRECT launches as it goes; MQ_PREPARE reserves
+    // scratch, uploads the arrays built on the host and reads back table values, with no
+    // device work; MQ_CAPTURE then enqueues only device work (kernels, memsets), into a
+    // CUDA graph, and must not grow any scratch
+    int mq_mode = 0;
+    u64 mq_p2_pv[2] = {0, 0};   // pi values mq_p2 needs, read in the prepare pass
+    void* mq_hard_kern = nullptr;   // the batched sieve's instantiation and resident CTAs per SM,
+    int mq_hard_per_sm = 0;         // chosen (and its shared-memory limit set) before any capture
 };
+
+enum { MQ_DIRECT = 0, MQ_PREPARE = 1, MQ_CAPTURE = 2 };
+inline bool mq_device_work(const pc_ctx* c) { return c->mq_mode != MQ_PREPARE; }
+inline bool mq_host_upload(const pc_ctx* c) { return c->mq_mode != MQ_CAPTURE; }
 
 u32 default_alpha(u64 x);
 int decimal_digits(u64 x);

@@ -670,9 +670,10 @@ int mq_s1_trivial(pc_ctx* ctx, const MQPlan& P)
     std::vector<u64> pref(P.Q + 1, 0);
     for (u32 q = 0; q < P.Q; q++) pref[q + 1] = pref[q] + P.hq[q].nlim;
     PC_TRY(buf_reserve(ctx, ctx->mq_pref, (P.Q + 1) * sizeof(u64)));
-    PC_CUDA(ctx, cudaMemcpyAsync(ctx->mq_pref.p, pref.data(), (P.Q + 1) * sizeof(u64), cudaMemcpyHostToDevice,
-                                 ctx->stream));
-    if (pref[P.Q] == 0) return PC_OK;
+    if (mq_host_upload(ctx))
+        PC_CUDA(ctx, cudaMemcpyAsync(ctx->mq_pref.p, pref.data(), (P.Q + 1) * sizeof(u64), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    if (pref[P.Q] == 0 || !mq_device_work(ctx)) return PC_OK;
     const int g = ctx->sm_count * 8;
     mq_s1_trivial_kernel<<<g, 256, 0, ctx->stream>>>(table_args(ctx), P.dq, ctx->mq_pref.as<u64>(), P.Q,
                                                      ctx->T.phiT[5].as<u32>(), 2310, P.parts);
@@ -746,7 +747,10 @@ int mq_easy(pc_ctx* ctx, const MQPlan& P)
     u32* nch = (u32*)(base + o_nch);
     u64* choff = (u64*)(base + o_off);
     unsigned long long* queue = (unsigned long long*)(base + o_q);
-    PC_CUDA(ctx, cudaMemcpyAsync(dpref, pref.data(), (P.Q + 1) * sizeof(u64), cudaMemcpyHostToDevice, ctx->stream));
+    if (mq_host_upload(ctx))
+        PC_CUDA(ctx, cudaMemcpyAsync(dpref, pref.data(), (P.Q + 1) * sizeof(u64), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    if (!mq_device_work(ctx)) return scan_exclusive_u32_to_u64(ctx, nch, choff, np);   // its scratch only
     PC_CUDA(ctx, cudaMemsetAsync(queue, 0, 64, ctx->stream));
     const LeafArgs T = table_args(ctx);
     mq_easy_ranges_kernel<<<(unsigned)((np + 255) / 256), 256, 0, ctx->stream>>>(T, P.dq, dpref, P.Q, rng, nch);

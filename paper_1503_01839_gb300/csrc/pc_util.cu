@@ -16,6 +16,10 @@ void pc_set_error(pc_ctx* ctx, const char* fmt, ...)
 int buf_reserve(pc_ctx* ctx, DevBuf& b, size_t bytes)
 {
     if (bytes <= b.bytes && b.p) return PC_OK;
+    if (ctx->mq_mode == MQ_CAPTURE) {   // captured nodes may already point at b.p
+        pc_set_error(ctx, "internal: scratch of %zu bytes grown during graph capture", bytes);
+        return PC_EINVAL;
+    }
     if (b.p) {
         cudaFree(b.p);
         b.p = nullptr;
@@ -163,6 +167,7 @@ static int scan_impl(pc_ctx* ctx, const u32* in, TO* out, u64 n)
     if (tiles == 0) tiles = 1;
     PC_TRY(buf_reserve(ctx, ctx->scan_tmp, (tiles + 1) * sizeof(TO)));
     TO* sums = ctx->scan_tmp.as<TO>();
+    if (!mq_device_work(ctx)) return PC_OK;
     scan_tile_sums<TO><<<(unsigned)tiles, SCAN_THREADS, 0, ctx->stream>>>(in, n, sums);
     PC_LAUNCHED(ctx);
     scan_sums_one_cta<TO><<<1, SCAN_THREADS, 0, ctx->stream>>>(sums, tiles);

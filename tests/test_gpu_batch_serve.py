@@ -32,6 +32,22 @@ def test_batch_mixed_sizes_match_alone_and_oracle(alone):
     assert st["kernel_launches"] > 0
 
 
+def test_batch_graph_equals_direct_launches(alone):
+    # the default runs the schedule's device work as one captured CUDA graph; the same
+    # kernels launched one by one, and every query alone, give the same results
+    xs = inputs.log_uniform_x(400, 7.0, 15.0, seed=31) + [1 << 20, 10 ** 10, 10 ** 15 - 1]
+    with pc.Context(0) as cg, pc.Context(0, batch_launch=1) as cd:
+        g1 = cg.pi_count_batch(xs)
+        sg = cg.stats()
+        g2 = cg.pi_count_batch(xs[::-1])   # a second graph on the same context
+        d = cd.pi_count_batch(xs)
+        sd = cd.stats()
+    assert g1 == d == g2[::-1]
+    assert g1 == [alone.pi_count(x) for x in xs]
+    assert sg["graph_launches"] == 1 and 10 <= sg["graph_nodes"] <= sg["kernel_launches"] + 8
+    assert sd["graph_launches"] == 0 and sd["graph_nodes"] == 0
+
+
 def test_batch_device_arrays_on_stream(alone):
     torch = pytest.importorskip("torch")
     xs = inputs.log_uniform_x(64, 6.0, 12.0, seed=12)
