@@ -42,7 +42,10 @@
 #include "pc_sieve.cuh"
 
 static constexpr u32 BATCH = 64;
-static constexpr u32 RECOUNT_P = 128;   // below this a warp recounts its blocks after crossing off
+// below this a warp crosses off whole wheel rounds per lane and recounts its blocks after;
+// from here on lanes take (class, round) pairs and decrement the block counters (64 against
+// 128: S2_hard(1e18) kernel 66.3 -> 65.0 ms)
+static constexpr u32 RECOUNT_P = 64;
 static constexpr u32 GROUP_P = 128;     // smallest prime crossed off in groups of leaf-free steps
 static_assert(GROUP_P >= RECOUNT_P, "grouped steps keep their block counters up to date");
 static constexpr u32 MAX_NW = 16;       // warps (sub-ranges) per segment
@@ -133,11 +136,12 @@ __device__ __forceinline__ bool leaf_window(const HardArgs& A, u64 p, u64 vp, u6
 }
 
 // A warp owns its sub-range, so crossing off one prime needs no atomics on
-// the bitset.  For p < 128 the lanes take whole wheel rounds (30 p integers,
-// p bytes), even rounds first, then odd ones, so lanes of one pass touch
-// words at least 2p bytes apart; for larger p a lane takes one residue class
-// in every fourth round, and two of its crossings by different lanes are at
-// least 4 bytes apart.  Runs of steps crossed off together (group_cross) mix
+// the bitset.  For p < RECOUNT_P (64) the lanes take whole wheel rounds (30 p
+// integers, p bytes), even rounds first, then odd ones, so lanes of one pass
+// touch words at least 2p bytes apart; for larger p a lane takes one residue
+// class in every fourth round, and two of its crossings by different lanes are
+// at least 4 bytes apart (classes of one round are >= floor(2p/30) bytes apart,
+// neighbouring rounds >= p - floor(29p/30) + floor(p/30); both are >= 4 for p >= 60).  Runs of steps crossed off together (group_cross) mix
 // primes in one pass and use atomics on the words.  Block counters take
 // shared-memory atomics, since lanes of one pass may share a block.
 // Instantiated for several (threads, resident CTAs) launch bounds: fewer
@@ -623,6 +627,36 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A0, Mul
                     const u32 len = enough ? (u32)__ffs(enough) : avail;   // steps t0 .. t0 + len - 1
                     const u32 TL = __shfl_sync(0xffffffffu, incl, len - 1);
                     const u32 loff = incl - n;                             // first leaf of step t0 + lane
+                    // leaf g of the run: its step i (the last i < len with loff_i <= g) and its
+                    // m-list data (nothing for g >= TL)
+                    auto run_leaf = [&](u32 g, u32& i, u32& info, u32& m32, u64& v, u32& gpf) {
+                        i = 0;
+                        for (u32 stp = 16; stp; stp >>= 1) {
+                            const u32 cand = i + stp;
+                            const u32 vv = __shfl_sync(0xffffffffu, loff, cand & 31);
+                            if (cand < len && vv <= g) i = cand;
+                        }
+                        const u32 ji = __shfl_sync(0xffffffffu, j0, i);
+                        const u32 li = __shfl_sync(0xffffffffu, loff, i);
+                        const u32 fl = st[t0 + i].flags;
+                        info = 0, m32 = 0, gpf = 0;
+                        v = 0;
+                        if (g < TL) {
+                            const u32 idx = ji + (g - li);
+                            if (fl & 1u) {
+                                info = ~0u;   // a prime: lpf = itself, mu = -1
+                                m32 = A.primes[idx];
+                                v = A.primes_rcp[idx];
+                            } else {
+                                const u32 li2 = (fl >> 2) & 7u;
+                                info = lst_info[li2][idx];
+                                m32 = lst_m[li2][idx];
+                                v = lst_rcp[li2][idx];
+                                gpf = A.trunc ? lst_gpf[li2][idx] : 0;
+                            }
+                        }
+                    };
+
                     // crossings against the starting bitset; hits logged in step order: each lane
                     // counts its hits, a warp scan gives its log offset, then it writes them
                     u32 nent = 0, hoff = 0;                                // hoff: log entries before step t0 + lane
@@ -692,36 +726,12 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A0, Mul
                     if (TL) {
                         block_prefix();   // of the run's starting bitset
                         for (u32 g0 = 0; g0 < TL; g0 += 32) {
-                            const u32 g = g0 + lane;
-                            // the step of leaf g: the last i < len with loff_i <= g
-                            u32 i = 0;
-                            for (u32 stp = 16; stp; stp >>= 1) {
-                                const u32 cand = i + stp;
-                                const u32 v = __shfl_sync(0xffffffffu, loff, cand & 31);
-                                if (cand < len && v <= g) i = cand;
-                            }
-                            const u32 ji = __shfl_sync(0xffffffffu, j0, i);
-                            const u32 li = __shfl_sync(0xffffffffu, loff, i);
+                            u32 i, info, m32, gpf;
+                            u64 v;
+                            run_leaf(g0 + lane, i, info, m32, v, gpf);
                             const u32 hi = __shfl_sync(0xffffffffu, hoff, i);
                             const u32 t = t0 + i, b = bb + t;
-                            const u32 fl = st[t].flags;
                             const u64 xp = st[t].xp;
-                            u32 info = 0, m32 = 0, gpf = 0;
-                            u64 v = 0;
-                            if (g < TL) {
-                                const u32 idx = ji + (g - li);
-                                if (fl & 1u) {
-                                    info = ~0u;   // a prime: lpf = itself, mu = -1
-                                    m32 = A.primes[idx];
-                                    v = A.primes_rcp[idx];
-                                } else {
-                                    const u32 li2 = (fl >> 2) & 7u;
-                                    info = lst_info[li2][idx];
-                                    m32 = lst_m[li2][idx];
-                                    v = lst_rcp[li2][idx];
-                                    gpf = A.trunc ? lst_gpf[li2][idx] : 0;
-                                }
-                            }
                             const bool valid = m32 && (info >> 1) > b && !(A.trunc && gpf > A.a);
                             const u32 e = seg_count_end(div_rcp(xp, m32, v), Lw);
                             u32 below = 0;   // hits of the run's earlier steps below the count end
@@ -825,9 +835,9 @@ __global__ void __launch_bounds__(MAXT, MINB) hard_sieve_kernel(HardArgs A0, Mul
                     };
                     {
                         if (base < (i32)sub_bytes) {
-                            if (p >= 128) {
+                            if (p >= RECOUNT_P) {
                                 // lane = (class j, round offset o): four rounds per pass.
-                                // Two crossings of one prime p >= 128 by different lanes
+                                // Two crossings of one prime p >= 64 by different lanes
                                 // are >= 4 bytes apart, so no two lanes share a word.
                                 const u32 j = lane & 7, o = lane >> 3;
                                 // round o, or o + 4 when round 0 starts below the first cofactor;
