@@ -384,12 +384,16 @@ def run_batch(local, n, streams, seed=0):
         t_tune = time.perf_counter() - t0
         tuned = {"1e%d" % (d - 1): cx.tuned(3 * 10 ** (d - 1)) + (cx.tuned_ctas(3 * 10 ** (d - 1)),)
                  for d in range(len(str(min(xs))), len(str(max(xs))) + 1)}
+        t0 = time.perf_counter()
+        cx.autotune_batch(xs)                      # the schedule's sieve segment size and residency
+        t_tune_b = time.perf_counter() - t0
         cx.pi_count_batch(xs)                      # builds and warms the shared tables
         t0 = time.perf_counter()
         got = cx.pi_count_batch(xs)
         tb = time.perf_counter() - t0
         bst = cx.stats()
         launches = bst["kernel_launches"]
+        cx_tuned_batch = cx.tuned_batch()
         t0 = time.perf_counter()
         plain = [cx.pi_count(v) for v in xs]
         tl = time.perf_counter() - t0
@@ -400,7 +404,8 @@ def run_batch(local, n, streams, seed=0):
             "slots": streams, "batch_s": tb, "batch_qps": n / tb, "plain_loop_s": tl, "plain_qps": n / tl,
             "speedup": tl / tb, "bit_exact": True, "gpu_launches": launches,
             "graph_launches": bst["graph_launches"], "graph_nodes": bst["graph_nodes"],
-            "autotune_s": t_tune, "tuned_alpha_seg_ctas_per_decade": tuned}
+            "autotune_s": t_tune, "tuned_alpha_seg_ctas_per_decade": tuned,
+            "autotune_batch_s": t_tune_b, "tuned_batch_seg_ctas": cx_tuned_batch}
 
 
 def run_serve(local, n, rate, streams, lo_exp=9.0, hi_exp=17.0, check=64, policy=0):

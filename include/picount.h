@@ -203,6 +203,22 @@ int pc_autotune(pc_ctx* ctx, uint64_t x_lo, uint64_t x_hi, uint32_t reps);
 /* The alpha and segment bytes pc_pi_count(x, 0) uses now. */
 int pc_tuned(pc_ctx* ctx, uint64_t x, uint32_t* alpha, uint32_t* seg_bytes);
 
+/* Autotuner of the batched schedule (pc_pi_count_batch): its one hard-leaf sieve
+ * launch over every query's segments shares one segment size and residency, which
+ * the per-decade tuning of pc_autotune cannot pick.  Runs the batch xs[0..n) with
+ * hard-leaf segments of 16 or 32 KiB and as many resident CTAs per SM as fit, 4 or
+ * 8 (16 KiB) or 2 (32 KiB), reps + 1 times each (the first untimed; reps 0 = 1),
+ * and keeps the fastest geometry in ctx for later batches.  Run pc_autotune first:
+ * alpha stays per query.  Every candidate's results must agree (else
+ * PC_EOVERFLOW and the default geometry).  A fixed pc_params seg_bytes or
+ * ctas_per_sm is kept fixed.  The paper schedules blocks dynamically by their
+ * measured run times (Section 3); here the geometry is measured, the schedule
+ * planned on the device. */
+int pc_autotune_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint32_t reps);
+/* The batched schedule's sieve geometry now: segment bytes and resident CTAs per SM
+ * (0 = as many as fit). */
+int pc_tuned_batch(pc_ctx* ctx, uint32_t* seg_bytes, uint32_t* ctas_per_sm);
+
 /* ---------------------------------------------------------------------------
  * Served queries: continuous batching over the context's tables.
  *

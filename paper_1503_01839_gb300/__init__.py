@@ -21,7 +21,7 @@ SYMBOLS = ["pc_create", "pc_destroy", "pc_set_stream", "pc_pi_count", "pc_phi", 
            "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats", "pc_strerror", "pc_last_error", "pc_version",
            "pc_p2_noalloc", "pc_server_create", "pc_server_submit", "pc_server_poll", "pc_server_get_stats",
            "pc_server_footprint", "pc_server_destroy", "pc_autotune", "pc_tuned", "pc_s2_hard_shard",
-           "pc_phi_starts", "pc_tuned_ctas"]
+           "pc_phi_starts", "pc_tuned_ctas", "pc_autotune_batch", "pc_tuned_batch"]
 
 PC_QUERY_PI = 0
 PC_QUERY_PHI = 1
@@ -124,12 +124,15 @@ def lib():
             L.pc_phi_starts.argtypes = [p, u64, u32, u64, ctypes.POINTER(u64)]
             L.pc_tuned.argtypes = [p, u64, ctypes.POINTER(u32), ctypes.POINTER(u32)]
             L.pc_tuned_ctas.argtypes = [p, u64, ctypes.POINTER(u32)]
+            L.pc_autotune_batch.argtypes = [p, p, ctypes.c_size_t, u32]
+            L.pc_tuned_batch.argtypes = [p, ctypes.POINTER(u32), ctypes.POINTER(u32)]
             L.pc_server_destroy.argtypes = [p]
             L.pc_server_destroy.restype = None
             for name in ("pc_create", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
                          "pc_leaf_sums", "pc_pi_count_batch", "pc_last_stats", "pc_server_create",
                          "pc_server_submit", "pc_server_poll", "pc_server_get_stats", "pc_autotune", "pc_tuned",
-                         "pc_s2_hard_shard", "pc_phi_starts", "pc_tuned_ctas"):
+                         "pc_s2_hard_shard", "pc_phi_starts", "pc_tuned_ctas", "pc_autotune_batch",
+                         "pc_tuned_batch"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -237,6 +240,16 @@ class Context:
         a, s = ctypes.c_uint32(), ctypes.c_uint32()
         self._check(self._L.pc_tuned(self._h, x, ctypes.byref(a), ctypes.byref(s)))
         return a.value, s.value
+
+    def autotune_batch(self, xs, reps: int = 0) -> None:
+        n = len(xs)
+        arr = (ctypes.c_uint64 * n)(*xs)
+        self._check(self._L.pc_autotune_batch(self._h, arr, n, reps))
+
+    def tuned_batch(self) -> tuple:
+        s, c = ctypes.c_uint32(), ctypes.c_uint32()
+        self._check(self._L.pc_tuned_batch(self._h, ctypes.byref(s), ctypes.byref(c)))
+        return s.value, c.value
 
     def tuned_ctas(self, x: int) -> int:
         v = ctypes.c_uint32()

@@ -728,6 +728,65 @@ extern "C" int pc_autotune(pc_ctx* ctx, uint64_t x_lo, uint64_t x_hi, uint32_t r
     return PC_OK;
 }
 
+// The batched schedule's sieve geometry: every candidate (hard-leaf segments of 16 or 32 KiB,
+// resident CTAs per SM as many as fit, 4 or 8) runs the whole batch reps + 1 times (the
+// first untimed), the results must agree, and the fastest is kept for later batches.
+extern "C" int pc_autotune_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint32_t reps)
+{
+    if (!ctx || (n && !xs) || ctx->borrowed) return PC_EINVAL;
+    if (n == 0) return PC_OK;
+    if (reps == 0) reps = 1;
+    struct Cand {
+        u32 seg, ctas;
+    };
+    static const Cand cands[] = {{16384, 0}, {16384, 4}, {16384, 8}, {32768, 0}, {32768, 2}};
+    std::vector<uint64_t> want(n), got(n);
+    double best_ms = 1e300;
+    Cand best = {0, 0};
+    bool have = false;
+    for (const Cand& c : cands) {
+        if (ctx->params.seg_bytes && c.seg != 16384) continue;   // a fixed segment size stays fixed
+        if (ctx->params.ctas_per_sm && c.ctas) continue;
+        ctx->batch_seg = c.seg;
+        ctx->batch_ctas = c.ctas;
+        double ms = 1e300;
+        for (u32 r = 0; r <= reps; r++) {
+            const auto t0 = std::chrono::steady_clock::now();
+            const int rc = pc_pi_count_batch(ctx, xs, n, got.data(), nullptr);
+            const double dt = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (rc != PC_OK) {
+                ctx->batch_seg = ctx->batch_ctas = 0;
+                return rc;
+            }
+            if (!have) {
+                want = got;
+                have = true;
+            } else if (got != want) {
+                ctx->batch_seg = ctx->batch_ctas = 0;
+                pc_set_error(ctx, "autotune_batch: results differ between settings (segment %u, %u CTAs per SM)",
+                             c.seg, c.ctas);
+                return PC_EOVERFLOW;
+            }
+            if (r && dt < ms) ms = dt;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    ctx->batch_seg = best.seg;
+    ctx->batch_ctas = best.ctas;
+    return PC_OK;
+}
+
+extern "C" int pc_tuned_batch(pc_ctx* ctx, uint32_t* seg_bytes, uint32_t* ctas_per_sm)
+{
+    if (!ctx || !seg_bytes || !ctas_per_sm) return PC_EINVAL;
+    *seg_bytes = ctx->params.seg_bytes ? ctx->params.seg_bytes : (ctx->batch_seg ? ctx->batch_seg : 16384);
+    *ctas_per_sm = ctx->params.ctas_per_sm ? ctx->params.ctas_per_sm : ctx->batch_ctas;
+    return PC_OK;
+}
+
 extern "C" int pc_tuned_ctas(pc_ctx* ctx, uint64_t x, uint32_t* ctas_per_sm)
 {
     if (!ctx || !ctas_per_sm) return PC_EINVAL;

@@ -1611,7 +1611,7 @@ int mq_hard(pc_ctx* ctx, const MQPlan& P)
     HardArgs T{};   // what every query of the batch shares: tables, geometry, queue, counters
     T.k0 = 5;
     T.kleaf = 5;
-    T.seg_bytes = pc_seg_bytes(ctx, 16384);
+    T.seg_bytes = pc_seg_bytes(ctx, ctx->batch_seg ? ctx->batch_seg : 16384);
     T.sub_bytes = pc_sub_bytes(ctx, T.seg_bytes);
     T.nw = T.seg_bytes / T.sub_bytes;
     T.sub_shift = 3;
@@ -1712,7 +1712,10 @@ int mq_hard(pc_ctx* ctx, const MQPlan& P)
     if (ctx->mq_mode != MQ_CAPTURE) {
         void (*kern)(HardArgs, MultiArgs) = nullptr;
         int per_sm = 0;
-        PC_TRY(choose_hard_kernel<true>(ctx, T, smem, &kern, &per_sm));
+        ctx->ctas_call = ctx->batch_ctas;   // the batch's tuned residency (0: as many as fit)
+        const int rc = choose_hard_kernel<true>(ctx, T, smem, &kern, &per_sm);
+        ctx->ctas_call = 0;
+        PC_TRY(rc);
         ctx->mq_hard_kern = (void*)kern;
         ctx->mq_hard_per_sm = per_sm;
     }

@@ -140,6 +140,9 @@ struct pc_ctx {
     // CUDA graph, and must not grow any scratch
     int mq_mode = 0;
     u64 mq_p2_pv[2] = {0, 0};   // pi values mq_p2 needs, read in the prepare pass
+    // hard-leaf sieve geometry of the batched schedule (pc_autotune_batch; 0 = default:
+    // 16 KiB segments, as many resident CTAs per SM as fit)
+    u32 batch_seg = 0, batch_ctas = 0;
     void* mq_hard_kern = nullptr;   // the batched sieve's instantiation and resident CTAs per SM,
     int mq_hard_per_sm = 0;         // chosen (and its shared-memory limit set) before any capture
 };

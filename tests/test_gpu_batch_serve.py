@@ -48,6 +48,23 @@ def test_batch_graph_equals_direct_launches(alone):
     assert sd["graph_launches"] == 0 and sd["graph_nodes"] == 0
 
 
+def test_autotune_batch_keeps_results(alone):
+    # the batch geometry tuner (segment size, resident CTAs) changes no result
+    xs = inputs.log_uniform_x(300, 8.0, 14.0, seed=32)
+    with pc.Context(0) as cx:
+        assert cx.tuned_batch() == (16384, 0)
+        before = cx.pi_count_batch(xs)
+        cx.autotune_batch(xs, reps=1)
+        seg, ctas = cx.tuned_batch()
+        assert (seg, ctas) in [(16384, 0), (16384, 4), (16384, 8), (32768, 0), (32768, 2)]
+        after = cx.pi_count_batch(xs[::-1])[::-1]
+    assert before == after == [alone.pi_count(x) for x in xs]
+    with pc.Context(0, seg_bytes=65536) as cf:   # a fixed segment size stays fixed
+        cf.autotune_batch(xs[:50], reps=1)
+        assert cf.tuned_batch()[0] == 65536
+        assert cf.pi_count_batch(xs[:50]) == before[:50]
+
+
 def test_batch_device_arrays_on_stream(alone):
     torch = pytest.importorskip("torch")
     xs = inputs.log_uniform_x(64, 6.0, 12.0, seed=12)
