@@ -81,6 +81,15 @@ typedef struct pc_params {
                              device work of every phase captured into one CUDA
                              graph and launched once (the default); 1 = the same
                              kernels launched one by one */
+    uint32_t p2_bucket;   /* the P2 sieve of pc_pi_count / pc_p2: 0 = every segment
+                             visits every sieving prime (the default); 1 = the
+                             bucket sieve of Section 2.3: segments of seg_bytes
+                             (default 4096 = 2^15 bits) taken in waves, and each
+                             prime p > seg_bytes (at most one multiple per residue
+                             class in a segment) visits only the segments holding
+                             its multiples, filed in per-segment buckets before
+                             each wave.  Same results.  The batch keeps the
+                             default. */
 } pc_params;
 
 /* Counters and phase times of the last successful call. */

@@ -40,7 +40,7 @@ class PcParams(ctypes.Structure):
     _fields_ = [("seg_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("threads", ctypes.c_uint32),
                 ("alpha", ctypes.c_uint32), ("c", ctypes.c_uint32), ("warp_bytes", ctypes.c_uint32),
                 ("streams", ctypes.c_uint32), ("pi_gather", ctypes.c_uint32), ("m_source", ctypes.c_uint32),
-                ("batch_launch", ctypes.c_uint32)]
+                ("batch_launch", ctypes.c_uint32), ("p2_bucket", ctypes.c_uint32)]
 
 
 class PcStats(ctypes.Structure):
@@ -149,10 +149,10 @@ class Context:
 
     def __init__(self, device: int = 0, seg_bytes: int = 0, ctas_per_sm: int = 0, threads: int = 0,
                  alpha: int = 0, c: int = 0, warp_bytes: int = 0, streams: int = 0, pi_gather: int = 0,
-                 m_source: int = 0, batch_launch: int = 0):
+                 m_source: int = 0, batch_launch: int = 0, p2_bucket: int = 0):
         self._L = lib()
         prm = PcParams(seg_bytes, ctas_per_sm, threads, alpha, c, warp_bytes, streams, pi_gather, m_source,
-                       batch_launch)
+                       batch_launch, p2_bucket)
         h = ctypes.c_void_p()
         rc = self._L.pc_create(ctypes.byref(h), device, ctypes.byref(prm))
         if rc != PC_OK:

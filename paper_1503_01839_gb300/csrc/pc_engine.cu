@@ -46,7 +46,7 @@ extern "C" int pc_create(pc_ctx** out, int device, const pc_params* p)
     const uint32_t wb = ctx->params.warp_bytes;
     if (ctx->params.c > 7 || (sb && sb != 1024 && sb != 2048 && (sb % 4096 || sb > 131072)) ||
         (wb && wb != 1024 && wb != 2048 && wb != 4096 && wb != 8192) ||
-        ctx->params.ctas_per_sm > 4 || ctx->params.pi_gather > 1 || ctx->params.m_source > 1 || ctx->params.batch_launch > 1 ||
+        ctx->params.ctas_per_sm > 4 || ctx->params.pi_gather > 1 || ctx->params.m_source > 1 || ctx->params.batch_launch > 1 || ctx->params.p2_bucket > 1 ||
         (ctx->params.threads && (ctx->params.threads % 32 || ctx->params.threads < 128 || ctx->params.threads > 1024))) {
         delete ctx;
         return PC_EINVAL;
@@ -81,7 +81,8 @@ extern "C" void pc_destroy(pc_ctx* ctx)
     DevBuf* bufs[] = {&ctx->seg_b, &ctx->seg_off, &ctx->counts, &ctx->tallies,
                       &ctx->acc_seg, &ctx->partials, &ctx->result, &ctx->misc, &ctx->scan_tmp, &ctx->queue,
                       &ctx->easy_rng, &ctx->easy_chunk_off, &ctx->easy_cmap, &ctx->starts,
-                      &ctx->mq_q, &ctx->mq_pref, &ctx->mq_e, &ctx->mq_h, &ctx->mq_hq, &ctx->mq_p};
+                      &ctx->mq_q, &ctx->mq_pref, &ctx->mq_e, &ctx->mq_h, &ctx->mq_hq, &ctx->mq_p,
+                      &ctx->p2_bkt};
     for (DevBuf* b : bufs) buf_free(*b);
     if (!ctx->borrowed) {
         Tables& T = ctx->T;

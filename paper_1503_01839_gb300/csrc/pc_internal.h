@@ -112,6 +112,7 @@ struct pc_ctx {
     DevBuf seg_b, seg_off, counts, tallies, acc_seg, partials, result, misc, scan_tmp, queue;
     DevBuf easy_rng, easy_chunk_off, easy_cmap, starts;
     DevBuf mq_q, mq_pref, mq_e, mq_h, mq_hq, mq_p;   // batched queries (pc_pi_count_batch)
+    DevBuf p2_bkt;   // P2 bucket sieve: the buckets of one wave of segments and their fill counts
     // pinned host staging for small results
     void* host_stage = nullptr;
     pc_stats stats{};

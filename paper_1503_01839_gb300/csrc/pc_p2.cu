@@ -29,6 +29,13 @@ struct P2Args {
     u32* queue;
     unsigned long long* stat;   // [3]: multiples crossed off (or null)
     const u32* pat;   // presieve pattern of the primes 7..19 (k0 = 8), or null (7 and 11 from patw)
+    // bucket sieve (Section 2.3), or null: the primes p_b, b >= b_bkt, are not visited by every
+    // segment; segment s crosses off only the bit positions filed in its bucket,
+    // bkt[s * bkt_cap + i] for i < bkt_n[s]
+    const u32* bkt;
+    const u32* bkt_n;
+    u32 bkt_cap;
+    u32 b_bkt;
 };
 
 // Primes below P2_COOP_P have many wheel rounds per segment and are crossed
@@ -163,12 +170,22 @@ __global__ void __launch_bounds__(NT, 3) p2_sieve_kernel(P2Args A0, P2Multi M)
             ncl += P2_NARROW && p < (1u << 29) ? p2_cross_class(bits, A.seg_bytes, L, (u32)p, ks, task & 7)
                              : cross_off_class(bits, A.seg_bytes, L, (u32)p, ks, task & 7, none);
         }
-        for (u32 bb = A.b_big + tid; bb <= A.B; bb += NT) {
+        const u32 b_end = A.bkt ? A.b_bkt : A.B + 1;
+        for (u32 bb = A.b_big + tid; bb < b_end; bb += NT) {
             const u64 p = A.primes[bb];
             u64 ks = L ? div_rcp(L + p - 1, p, A.primes_rcp[bb]) : 0;
             if (ks < p) ks = p;
             ncl += P2_NARROW && p < (1u << 29) ? p2_cross_single(bits, A.seg_bytes, L, (u32)p, ks)
                              : cross_off_single(bits, A.seg_bytes, L, (u32)p, ks, none);
+        }
+        if (A.bkt) {   // the larger primes: only the multiples filed in this segment's bucket
+            const u32 nf = pc_min(A.bkt_n[s], A.bkt_cap);
+            const u32* e = A.bkt + s * A.bkt_cap;
+            for (u32 i = tid; i < nf; i += NT) {
+                const u32 pos = e[i];
+                atomicAnd(&bits[pos >> 5], ~(1u << (pos & 31)));
+                ncl++;
+            }
         }
         // the sieving primes themselves (only in the first segments)
         for (u32 bb = A.k0 + 1 + tid; bb <= A.B; bb += NT) {
@@ -331,6 +348,147 @@ __global__ void p2_constant_kernel(u64 K, u64 a, u64 B, I128Pair* out)
     store_i128(out, load_i128(out) + n * (i128)(B - 1) - sum_k1);
 }
 
+// ------------------------------------------------------------- bucket sieve
+// Section 2.3 suggests a bucket sieve: each sieving prime waits in the bucket of the next
+// interval that holds one of its multiples, so an interval meets only the primes that cross
+// something off in it.  Here the buckets are filled a wave of segments at a time: one
+// thread per (prime, residue class) walks the class's multiples k p (k >= p) inside the wave
+// and files each under its segment; the sieve kernel then applies them.  The primes taken
+// this way are those above the segment's bytes, which have at most one multiple per residue
+// class in a segment.
+
+// Bound on the entries one segment's bucket can receive: a prime p has at most
+// floor((span - 1) / p) + 1 multiples among span consecutive integers, at most 8 of them
+// with a cofactor coprime to 30 (any 30 consecutive integers hold 8 such).  One CTA.
+__global__ void p2_bucket_bound_kernel(P2Args A, unsigned long long* out)
+{
+    __shared__ unsigned long long part[32];
+    unsigned long long s = 0;
+    for (u32 b = A.b_bkt + threadIdx.x; b <= A.B; b += blockDim.x) {
+        const u64 m = (A.span - 1) / A.primes[b] + 1;
+        s += m < 8 ? m : 8;
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (u32 w = 0; w < blockDim.x / 32; w++) t += part[w];
+        *out = t;
+    }
+}
+
+// Files the multiples k p (k >= p, k = R8[j] mod 30) of the bucket primes that lie in the
+// segments w0 .. w0 + W - 1 of A (W * span < 2^32, W <= P2_WAVE_MAX): thread per (prime p_b,
+// class j).  A CTA first counts its entries per segment in shared memory, reserves a range
+// of every segment's bucket with one global atomic, then files its entries there, so the
+// global atomics do not grow with the entries.  A full bucket sets *err and drops the entry
+// (the bound of p2_bucket_bound_kernel rules that out).
+static constexpr u32 P2_WAVE_MAX = 4096;
+__global__ void __launch_bounds__(256) p2_bucket_fill_kernel(P2Args A, u64 w0, u32 W, u32* bkt, u32* bkt_n,
+                                                             u32 cap, int* err)
+{
+    __shared__ u32 hist[P2_WAVE_MAX], base[P2_WAVE_MAX];
+    for (u32 i = threadIdx.x; i < W; i += blockDim.x) hist[i] = 0;
+    const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 Lw = (A.s0 + w0) * A.span;   // the wave's first integer
+    const u32 wspan = W * (u32)A.span;     // its length
+    u32 rel0 = wspan, step = 0;            // first offset in the wave (wspan: none)
+    if (t < 8ull * (A.B + 1 - A.b_bkt)) {
+        const u32 b = A.b_bkt + (u32)(t >> 3), j = (u32)(t & 7);
+        const u64 p = A.primes[b];
+        u64 k = Lw ? div_rcp(Lw + p - 1, p, A.primes_rcp[b]) : 0;
+        if (k < p) k = p;
+        const u32 rj = r8(j);
+        u64 q = k / 30;
+        if (30 * q + rj < k) q++;
+        const u64 n0 = (30 * q + rj) * p;
+        if (n0 - Lw < wspan) rel0 = (u32)(n0 - Lw);
+        step = 30 * (u32)p;
+    }
+    __syncthreads();
+    const u32 sp = (u32)A.span;
+    for (u64 rel = rel0; rel < wspan; rel += step) atomicAdd(&hist[(u32)rel / sp], 1u);
+    __syncthreads();
+    for (u32 i = threadIdx.x; i < W; i += blockDim.x) {
+        const u32 h = hist[i];
+        base[i] = h ? atomicAdd(&bkt_n[i], h) : 0;
+        hist[i] = 0;
+    }
+    __syncthreads();
+    for (u64 rel = rel0; rel < wspan; rel += step) {
+        const u32 sl = (u32)rel / sp, r = (u32)rel - sl * sp;
+        const u32 pos = (r / 30) * 8 + idx30(r % 30);
+        const u32 slot = base[sl] + atomicAdd(&hist[sl], 1u);
+        if (slot < cap) bkt[(u64)sl * cap + slot] = pos;
+        else *err = 1;
+    }
+}
+
+// The sieve of P2 with bucket primes: waves of W segments, each with its buckets filed
+// first; W from the bound on a bucket's entries and a budget of 2^26 entries (256 MiB), so
+// the buckets' memory does not grow with the number of segments.
+static int run_p2_buckets(pc_ctx* ctx, const P2Args& A, int ctas, size_t smem)
+{
+    PC_TRY(buf_reserve(ctx, ctx->p2_bkt, 256));
+    p2_bucket_bound_kernel<<<1, 1024, 0, ctx->stream>>>(A, ctx->p2_bkt.as<unsigned long long>());
+    PC_LAUNCHED(ctx);
+    u64 cap = 0;
+    PC_TRY(copy_to_host(ctx, &cap, ctx->p2_bkt.p, sizeof(u64)));
+    // bucket entries per wave: 2^26 (256 MiB; pi(1e18)'s P2 at 4 KiB segments 70.7 ms with
+    // 2^24, 57.9 with 2^26, 55.6 with 2^27)
+    constexpr u64 P2_BKT_BUDGET = 1ull << 26;
+    if (cap == 0 || cap > P2_BKT_BUDGET) {
+        pc_set_error(ctx, "p2 buckets: %llu entries per segment", (unsigned long long)cap);
+        return PC_EINVAL;
+    }
+    u64 W = P2_BKT_BUDGET / cap;
+    W = pc_min(W, A.nseg);
+    W = pc_min(W, (u64)0xFFFFFFFFu / A.span);   // the fill kernel's offsets inside a wave are 32-bit
+    W = pc_min(W, (u64)P2_WAVE_MAX);              // and its per-segment counters fit in shared memory
+    if (W == 0) W = 1;
+    const size_t o_n = ((size_t)(W * cap * sizeof(u32)) + 255) / 256 * 256;
+    const size_t o_err = o_n + ((size_t)W * sizeof(u32) + 255) / 256 * 256;
+    PC_TRY(buf_reserve(ctx, ctx->p2_bkt, o_err + 256));
+    unsigned char* base = ctx->p2_bkt.as<unsigned char>();
+    u32* d_bkt = (u32*)base;
+    u32* d_n = (u32*)(base + o_n);
+    int* d_err = (int*)(base + o_err);
+    PC_CUDA(ctx, cudaMemsetAsync(d_err, 0, sizeof(int), ctx->stream));
+    const u64 threads = 8ull * (A.B + 1 - A.b_bkt);
+    PC_CUDA(ctx, cudaEventRecord(ctx->ev[4], ctx->stream));
+    for (u64 w0 = 0; w0 < A.nseg; w0 += W) {
+        const u32 Wc = (u32)pc_min(W, A.nseg - w0);
+        PC_CUDA(ctx, cudaMemsetAsync(d_n, 0, Wc * sizeof(u32), ctx->stream));
+        p2_bucket_fill_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(A, w0, Wc, d_bkt, d_n,
+                                                                                          (u32)cap, d_err);
+        PC_LAUNCHED(ctx);
+        PC_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 64, ctx->stream));
+        P2Args Aw = A;
+        Aw.s0 = A.s0 + w0;
+        Aw.nseg = Wc;
+        Aw.cnt = A.cnt + w0;
+        Aw.tally = A.tally + w0;
+        Aw.acc = A.acc + w0;
+        Aw.bkt = d_bkt;
+        Aw.bkt_n = d_n;
+        Aw.bkt_cap = (u32)cap;
+        p2_sieve_kernel<512, false><<<(unsigned)pc_min((u64)ctas, (u64)Wc), 512, smem, ctx->stream>>>(Aw,
+                                                                                                     P2Multi{});
+        PC_LAUNCHED(ctx);
+        ctx->stats.kernel_launches += 2;
+    }
+    PC_CUDA(ctx, cudaEventRecord(ctx->ev[5], ctx->stream));
+    int err = 0;
+    PC_TRY(copy_to_host(ctx, &err, d_err, sizeof(int)));
+    if (err) {
+        pc_set_error(ctx, "p2 buckets: a bucket overflowed its bound (internal)");
+        return PC_EOVERFLOW;
+    }
+    ctx->stats.kernel_launches += 1;
+    return PC_OK;
+}
+
 int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
 {
     const u64 r = pc_isqrt(x);
@@ -364,7 +522,9 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     // 32 KiB segments up to z = 2^30, 64 KiB up to 2^32, 48 KiB beyond (measured on
     // GB300: the small segments win by a third at z ~ 1e8 and lose a few percent at
     // z ~ 1.5e9; 48 KiB against 64 KiB: pi(1e17) P2 2.45 -> 2.38 ms, pi(1e18) 8.9 -> 8.5 ms)
-    A.seg_bytes = pc_seg_bytes(ctx, A.z < (1ull << 30) ? 32768 : A.z < (1ull << 32) ? 65536 : 49152);
+    const bool bucket = ctx->params.p2_bucket != 0;
+    A.seg_bytes = bucket ? pc_seg_bytes(ctx, 4096)
+                         : pc_seg_bytes(ctx, A.z < (1ull << 30) ? 32768 : A.z < (1ull << 32) ? 65536 : 49152);
     A.span = 30ull * A.seg_bytes;
     {
         u64 v2[2] = {P2_COOP_P - 1, A.seg_bytes / 8}, pv2[2];
@@ -374,6 +534,15 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     }
     A.s0 = r / A.span;                   // r <= z since y < r
     A.nseg = z / A.span + 1 - A.s0;
+    A.bkt = nullptr;
+    A.bkt_n = nullptr;
+    A.bkt_cap = 0;
+    A.b_bkt = (u32)B + 1;
+    if (bucket) {   // bucket primes: p > seg_bytes, at most one multiple per residue class in a segment
+        u64 v1 = A.seg_bytes, pv1 = 0;
+        PC_TRY(tables_pi_values(ctx, &v1, &pv1, 1));
+        A.b_bkt = (u32)pc_min(pc_max(pv1 + 1, (u64)A.b_big), B + 1);
+    }
     A.pit = ctx->T.pi();
     A.primes = ctx->T.primes.as<u32>();
     A.primes_rcp = ctx->T.primes_rcp.as<u64>();
@@ -407,10 +576,14 @@ int run_p2(pc_ctx* ctx, u64 x, u64 y, u64 a, I128Pair* out)
     int ctas = ctx->sm_count * per_sm;
     if ((u64)ctas > A.nseg) ctas = (int)A.nseg;
     A.stat = ctx->dstat;
-    PC_CUDA(ctx, cudaEventRecord(ctx->ev[4], ctx->stream));
-    p2_sieve_kernel<512, false><<<ctas, 512, smem, ctx->stream>>>(A, P2Multi{});
-    PC_LAUNCHED(ctx);
-    PC_CUDA(ctx, cudaEventRecord(ctx->ev[5], ctx->stream));
+    if (A.b_bkt <= B) {
+        PC_TRY(run_p2_buckets(ctx, A, ctas, smem));
+    } else {
+        PC_CUDA(ctx, cudaEventRecord(ctx->ev[4], ctx->stream));
+        p2_sieve_kernel<512, false><<<ctas, 512, smem, ctx->stream>>>(A, P2Multi{});
+        PC_LAUNCHED(ctx);
+        PC_CUDA(ctx, cudaEventRecord(ctx->ev[5], ctx->stream));
+    }
     ctx->p2_timed = true;
     p2_combine_kernel<<<1, 1024, 0, ctx->stream>>>(A, out);
     PC_LAUNCHED(ctx);
