@@ -97,11 +97,12 @@ struct P2Multi {
     unsigned long long items;
 };
 
-// Three resident CTAs per SM (at most 42 registers a thread, no spills): the barriers
-// between a segment's phases then leave other CTAs to issue (17.0 against 18.8 ms at
-// pi(10^18) with two CTAs, and 27.9 ms with the one the registers allow when unbounded)
+// Four resident CTAs per SM (32 registers a thread, a few bytes spilled): the barriers
+// between a segment's phases then leave other CTAs to issue (P2 of pi(10^18) 7.8 ms against
+// 8.4 with three CTAs at 38 registers, 10.4 with two; earlier builds: 27.9 ms with the one
+// CTA the registers allowed when unbounded)
 template <int NT, bool MULTI>
-__global__ void __launch_bounds__(NT, 3) p2_sieve_kernel(P2Args A0, P2Multi M)
+__global__ void __launch_bounds__(NT, 4) p2_sieve_kernel(P2Args A0, P2Multi M)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u32* bits = (u32*)smem_raw;
