@@ -358,9 +358,10 @@ __global__ void p2_constant_kernel(u64 K, u64 a, u64 B, I128Pair* out)
 // this way are those above the segment's bytes, which have at most one multiple per residue
 // class in a segment.
 
-// Bound on the entries one segment's bucket can receive: a prime p has at most
-// floor((span - 1) / p) + 1 multiples among span consecutive integers, at most 8 of them
-// with a cofactor coprime to 30 (any 30 consecutive integers hold 8 such).  One CTA.
+// Bound on the entries one segment's bucket can receive: a prime p has m = floor((span - 1)
+// / p) + 1 or fewer multiples k p among span consecutive integers, with consecutive k; for
+// p > seg_bytes, m <= 30, and at most 8 of 30 consecutive k are coprime to 30, so at most
+// min(m, 8) of them are filed.  One CTA.
 __global__ void p2_bucket_bound_kernel(P2Args A, unsigned long long* out)
 {
     __shared__ unsigned long long part[32];
