@@ -405,7 +405,7 @@ def run_batch(local, n, streams, seed=0):
             "speedup": tl / tb, "bit_exact": True, "gpu_launches": launches,
             "graph_launches": bst["graph_launches"], "graph_nodes": bst["graph_nodes"],
             "autotune_s": t_tune, "tuned_alpha_seg_ctas_per_decade": tuned,
-            "autotune_batch_s": t_tune_b, "tuned_batch_seg_ctas": cx_tuned_batch}
+            "autotune_batch_s": t_tune_b, "tuned_batch_seg_ctas_builtin_alpha": cx_tuned_batch}
 
 
 def run_serve(local, n, rate, streams, lo_exp=9.0, hi_exp=17.0, check=64, policy=0):
@@ -499,8 +499,9 @@ def main():
     ap.add_argument("--no-pi", action="store_true", help="skip the pi(1e16)/pi(1e18) wall-time lines")
     ap.add_argument("--x", type=float, default=1e18, help="profiling only: a smaller x than the benchmark's")
     ap.add_argument("--alpha", type=int, default=20)
-    ap.add_argument("--mode", default="s2_hard", choices=["s2_hard", "pi", "batch", "serve"],
-                    help="pi / batch / serve: time only that part (profiling aid)")
+    ap.add_argument("--mode", default="s2_hard", choices=["s2_hard", "pi", "batch", "batch-graph", "serve"],
+                    help="pi / batch / serve: time only that part; batch-graph: only the batched call, "
+                         "twice, no tuning and no plain loop (profiling aids)")
     ap.add_argument("--batch", type=int, default=4096, help="queries of the batched workload (0: skip)")
     ap.add_argument("--serve", type=int, default=1000, help="requests of the served workload (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -516,6 +517,20 @@ def main():
         return run_pi_mode(args)
     if args.mode == "batch":
         print(json.dumps(run_batch(0, args.batch, args.streams)), flush=True)
+        return 0
+    if args.mode == "batch-graph":
+        import paper_1503_01839_gb300 as pc
+        from paper_1503_01839_gb300 import inputs
+        xs = inputs.batch_queries(args.batch, 0)
+        with pc.Context(0, streams=args.streams) as cx:
+            cx.pi_count_batch(xs)                  # builds the shared tables
+            t0 = time.perf_counter()
+            cx.pi_count_batch(xs)
+            dt = time.perf_counter() - t0
+            st = cx.stats()
+        print(json.dumps({"mode": "batch-graph", "queries": len(xs), "batch_s": dt, "qps": len(xs) / dt,
+                          "kernel_launches": st["kernel_launches"], "graph_launches": st["graph_launches"],
+                          "graph_nodes": st["graph_nodes"]}), flush=True)
         return 0
     if args.mode == "serve":
         for pol in (0, 1):

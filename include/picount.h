@@ -214,19 +214,19 @@ int pc_tuned(pc_ctx* ctx, uint64_t x, uint32_t* alpha, uint32_t* seg_bytes);
 
 /* Autotuner of the batched schedule (pc_pi_count_batch): its one hard-leaf sieve
  * launch over every query's segments shares one segment size and residency, which
- * the per-decade tuning of pc_autotune cannot pick.  Runs the batch xs[0..n) with
- * hard-leaf segments of 16 or 32 KiB and as many resident CTAs per SM as fit, 4 or
- * 8 (16 KiB) or 2 (32 KiB), reps + 1 times each (the first untimed; reps 0 = 1),
- * and keeps the fastest geometry in ctx for later batches.  Run pc_autotune first:
- * alpha stays per query.  Every candidate's results must agree (else
- * PC_EOVERFLOW and the default geometry).  A fixed pc_params seg_bytes or
- * ctas_per_sm is kept fixed.  The paper schedules blocks dynamically by their
+ * the per-decade tuning of pc_autotune cannot pick, and the alphas that suit single
+ * queries need not suit the batch's throughput.  Runs the batch xs[0..n) with the
+ * alphas of pc_autotune or the built-in ones, and hard-leaf segments of 16 KiB (as
+ * many resident CTAs per SM as fit, or 8) or 32 KiB (as many as fit), reps + 1
+ * times each (the first untimed; reps 0 = 1), and keeps the fastest in ctx for
+ * later batches.  Every candidate's results must agree (else PC_EOVERFLOW and the
+ * defaults).  A fixed pc_params alpha, seg_bytes or ctas_per_sm is kept fixed.  The paper schedules blocks dynamically by their
  * measured run times (Section 3); here the geometry is measured, the schedule
  * planned on the device. */
 int pc_autotune_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint32_t reps);
-/* The batched schedule's sieve geometry now: segment bytes and resident CTAs per SM
- * (0 = as many as fit). */
-int pc_tuned_batch(pc_ctx* ctx, uint32_t* seg_bytes, uint32_t* ctas_per_sm);
+/* The batched schedule's choice now: segment bytes, resident CTAs per SM (0 = as
+ * many as fit), and 1 if it uses the built-in alphas (0: pc_autotune's). */
+int pc_tuned_batch(pc_ctx* ctx, uint32_t* seg_bytes, uint32_t* ctas_per_sm, uint32_t* builtin_alpha);
 
 /* ---------------------------------------------------------------------------
  * Served queries: continuous batching over the context's tables.

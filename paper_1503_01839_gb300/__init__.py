@@ -125,7 +125,7 @@ def lib():
             L.pc_tuned.argtypes = [p, u64, ctypes.POINTER(u32), ctypes.POINTER(u32)]
             L.pc_tuned_ctas.argtypes = [p, u64, ctypes.POINTER(u32)]
             L.pc_autotune_batch.argtypes = [p, p, ctypes.c_size_t, u32]
-            L.pc_tuned_batch.argtypes = [p, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+            L.pc_tuned_batch.argtypes = [p, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)]
             L.pc_server_destroy.argtypes = [p]
             L.pc_server_destroy.restype = None
             for name in ("pc_create", "pc_set_stream", "pc_pi_count", "pc_phi", "pc_s2_hard", "pc_p2",
@@ -247,9 +247,10 @@ class Context:
         self._check(self._L.pc_autotune_batch(self._h, arr, n, reps))
 
     def tuned_batch(self) -> tuple:
-        s, c = ctypes.c_uint32(), ctypes.c_uint32()
-        self._check(self._L.pc_tuned_batch(self._h, ctypes.byref(s), ctypes.byref(c)))
-        return s.value, c.value
+        """(segment bytes, resident CTAs per SM, 1 if the built-in alphas) of the batch."""
+        s, c, a = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        self._check(self._L.pc_tuned_batch(self._h, ctypes.byref(s), ctypes.byref(c), ctypes.byref(a)))
+        return s.value, c.value, a.value
 
     def tuned_ctas(self, x: int) -> int:
         v = ctypes.c_uint32()

@@ -99,7 +99,14 @@ static u32 pi_small(u64 v)   // pi(v) for v < 17
     return t[v < 17 ? v : 16];
 }
 
-static void needs_pi(const pc_ctx* ctx, u64 x, TableNeeds& N)
+// alpha of a query of the batched schedule: the built-in table when pc_autotune_batch found it
+// faster for the batch than the per-decade alphas pc_autotune picked for single queries
+static u32 batch_alpha(const pc_ctx* ctx, u64 x)
+{
+    return ctx->batch_builtin_alpha && !ctx->params.alpha ? default_alpha(x) : choose_alpha(ctx, x);
+}
+
+static void needs_pi(const pc_ctx* ctx, u64 x, TableNeeds& N, bool batched = false)
 {
     if (x < 2) return;
     if (x < (1ull << 20)) {
@@ -107,7 +114,7 @@ static void needs_pi(const pc_ctx* ctx, u64 x, TableNeeds& N)
         return;
     }
     const u64 r = pc_isqrt(x);
-    u64 y = (u64)choose_alpha(ctx, x) * pc_iroot3(x);
+    u64 y = (u64)(batched ? batch_alpha(ctx, x) : choose_alpha(ctx, x)) * pc_iroot3(x);
     if (y > r) y = r;
     if (y < 1) y = 1;
     u32 c = ctx->params.c ? ctx->params.c : 5;
@@ -279,7 +286,7 @@ static int multi_batch(pc_ctx* ctx, const std::vector<u64>& xs, std::vector<u64>
     for (u32 k = 0; k < n; k++) {
         const u64 x = xs[order[k]];
         const u64 r = pc_isqrt(x);
-        u64 y = (u64)choose_alpha(ctx, x) * pc_iroot3(x);
+        u64 y = (u64)batch_alpha(ctx, x) * pc_iroot3(x);
         if (y > r) y = r;
         MQ& m = P.hq[k];
         memset(&m, 0, sizeof(m));
@@ -287,7 +294,7 @@ static int multi_batch(pc_ctx* ctx, const std::vector<u64>& xs, std::vector<u64>
         m.y = y;
         m.z = x / y;
         m.c = 5;   // pi(y) >= 5 for every x >= 2^20
-        needs_pi(ctx, x, N);
+        needs_pi(ctx, x, N, true);
     }
     PC_TRY(build_needs(ctx, N));
     // mq_q: queries (n MQ) | parts (5 n I128Pair) | results (n u64) | overflow flag
@@ -728,9 +735,10 @@ extern "C" int pc_autotune(pc_ctx* ctx, uint64_t x_lo, uint64_t x_hi, uint32_t r
     return PC_OK;
 }
 
-// The batched schedule's sieve geometry: every candidate (hard-leaf segments of 16 or 32 KiB,
-// resident CTAs per SM as many as fit, 4 or 8) runs the whole batch reps + 1 times (the
-// first untimed), the results must agree, and the fastest is kept for later batches.
+// The batched schedule's alphas and sieve geometry: every candidate (the per-decade alphas of
+// pc_autotune or the built-in ones; hard-leaf segments of 16 or 32 KiB, resident CTAs per SM
+// as many as fit or 8) runs the whole batch reps + 1 times (the first untimed), the results
+// must agree, and the fastest is kept for later batches.
 extern "C" int pc_autotune_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint32_t reps)
 {
     if (!ctx || (n && !xs) || ctx->borrowed) return PC_EINVAL;
@@ -738,17 +746,20 @@ extern "C" int pc_autotune_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint
     if (reps == 0) reps = 1;
     struct Cand {
         u32 seg, ctas;
+        bool builtin;
     };
-    static const Cand cands[] = {{16384, 0}, {16384, 4}, {16384, 8}, {32768, 0}, {32768, 2}};
+    static const Cand cands[] = {{16384, 0, false}, {16384, 8, false}, {32768, 0, false},
+                                 {16384, 0, true},  {16384, 8, true},  {32768, 0, true}};
     std::vector<uint64_t> want(n), got(n);
     double best_ms = 1e300;
-    Cand best = {0, 0};
+    Cand best = {0, 0, false};
     bool have = false;
     for (const Cand& c : cands) {
         if (ctx->params.seg_bytes && c.seg != 16384) continue;   // a fixed segment size stays fixed
         if (ctx->params.ctas_per_sm && c.ctas) continue;
         ctx->batch_seg = c.seg;
         ctx->batch_ctas = c.ctas;
+        ctx->batch_builtin_alpha = c.builtin;
         double ms = 1e300;
         for (u32 r = 0; r <= reps; r++) {
             const auto t0 = std::chrono::steady_clock::now();
@@ -756,6 +767,7 @@ extern "C" int pc_autotune_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint
             const double dt = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             if (rc != PC_OK) {
                 ctx->batch_seg = ctx->batch_ctas = 0;
+                ctx->batch_builtin_alpha = false;
                 return rc;
             }
             if (!have) {
@@ -763,6 +775,7 @@ extern "C" int pc_autotune_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint
                 have = true;
             } else if (got != want) {
                 ctx->batch_seg = ctx->batch_ctas = 0;
+                ctx->batch_builtin_alpha = false;
                 pc_set_error(ctx, "autotune_batch: results differ between settings (segment %u, %u CTAs per SM)",
                              c.seg, c.ctas);
                 return PC_EOVERFLOW;
@@ -776,12 +789,14 @@ extern "C" int pc_autotune_batch(pc_ctx* ctx, const uint64_t* xs, size_t n, uint
     }
     ctx->batch_seg = best.seg;
     ctx->batch_ctas = best.ctas;
+    ctx->batch_builtin_alpha = best.builtin;
     return PC_OK;
 }
 
-extern "C" int pc_tuned_batch(pc_ctx* ctx, uint32_t* seg_bytes, uint32_t* ctas_per_sm)
+extern "C" int pc_tuned_batch(pc_ctx* ctx, uint32_t* seg_bytes, uint32_t* ctas_per_sm, uint32_t* builtin_alpha)
 {
-    if (!ctx || !seg_bytes || !ctas_per_sm) return PC_EINVAL;
+    if (!ctx || !seg_bytes || !ctas_per_sm || !builtin_alpha) return PC_EINVAL;
+    *builtin_alpha = ctx->batch_builtin_alpha && !ctx->params.alpha ? 1u : 0u;
     *seg_bytes = ctx->params.seg_bytes ? ctx->params.seg_bytes : (ctx->batch_seg ? ctx->batch_seg : 16384);
     *ctas_per_sm = ctx->params.ctas_per_sm ? ctx->params.ctas_per_sm : ctx->batch_ctas;
     return PC_OK;

@@ -144,6 +144,7 @@ struct pc_ctx {
     // hard-leaf sieve geometry of the batched schedule (pc_autotune_batch; 0 = default:
     // 16 KiB segments, as many resident CTAs per SM as fit)
     u32 batch_seg = 0, batch_ctas = 0;
+    bool batch_builtin_alpha = false;   // the batch uses the built-in alphas, not pc_autotune's
     void* mq_hard_kern = nullptr;   // the batched sieve's instantiation and resident CTAs per SM,
     int mq_hard_per_sm = 0;         // chosen (and its shared-memory limit set) before any capture
 };
