@@ -57,6 +57,7 @@ def test_create_without_gpu_fails_cleanly(libpath):
 
 
 def test_bad_params_rejected_before_device_work(libpath):
-    with pytest.raises(pc.PicountError) as e:
-        pc.Context(0, seg_bytes=5120)
-    assert e.value.code == -1
+    for bad in ({"seg_bytes": 5120}, {"batch_launch": 2}, {"p2_bucket": 2}, {"m_source": 2}, {"pi_gather": 2}):
+        with pytest.raises(pc.PicountError) as e:
+            pc.Context(0, **bad)
+        assert e.value.code == -1, bad
