@@ -380,37 +380,61 @@ __global__ void p2_bucket_bound_kernel(P2Args A, unsigned long long* out)
     }
 }
 
+// Work of the fill: the multiples of one (prime, residue class) inside a wave are cut into
+// chunks of at most P2_FILL_CHUNK, one thread each, so that the threads of small primes (many
+// multiples per wave) do not hold up the launch.  pref[i] counts the threads of the bucket
+// primes before p_(b_bkt + i): 8 classes x ceil((floor(W span / (30 p)) + 1) / P2_FILL_CHUNK).
+static constexpr u32 P2_FILL_CHUNK = 64;
+__global__ void p2_bucket_chunks_kernel(P2Args A, u32 W, u32* nthr)
+{
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > A.B - A.b_bkt) return;
+    const u64 p = A.primes[A.b_bkt + i];
+    const u64 mult = (u64)W * A.span / (30 * p) + 1;   // multiples of one class in a wave, at most
+    nthr[i] = 8 * (u32)((mult + P2_FILL_CHUNK - 1) / P2_FILL_CHUNK);
+}
+
 // Files the multiples k p (k >= p, k = R8[j] mod 30) of the bucket primes that lie in the
-// segments w0 .. w0 + W - 1 of A (W * span < 2^32, W <= P2_WAVE_MAX): thread per (prime p_b,
-// class j).  A CTA first counts its entries per segment in shared memory, reserves a range
-// of every segment's bucket with one global atomic, then files its entries there, so the
-// global atomics do not grow with the entries.  A full bucket sets *err and drops the entry
-// (the bound of p2_bucket_bound_kernel rules that out).
+// segments w0 .. w0 + W - 1 of A (W * span < 2^32, W <= P2_WAVE_MAX): thread t takes chunk c
+// of (prime p_b, class j), found from pref (nb + 1 entries).  A CTA first counts its entries
+// per segment in shared memory, reserves a range of every segment's bucket with one global
+// atomic, then files its entries there, so the global atomics do not grow with the entries.
+// A full bucket sets *err and drops the entry (the bound of p2_bucket_bound_kernel rules that
+// out).
 static constexpr u32 P2_WAVE_MAX = 4096;
-__global__ void __launch_bounds__(256) p2_bucket_fill_kernel(P2Args A, u64 w0, u32 W, u32* bkt, u32* bkt_n,
-                                                             u32 cap, int* err)
+__global__ void __launch_bounds__(256) p2_bucket_fill_kernel(P2Args A, u64 w0, u32 W, const u32* pref, u32 nb,
+                                                             u32* bkt, u32* bkt_n, u32 cap, int* err)
 {
     __shared__ u32 hist[P2_WAVE_MAX], base[P2_WAVE_MAX];
     for (u32 i = threadIdx.x; i < W; i += blockDim.x) hist[i] = 0;
-    const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
     const u64 Lw = (A.s0 + w0) * A.span;   // the wave's first integer
     const u32 wspan = W * (u32)A.span;     // its length
-    u32 rel0 = wspan, step = 0;            // first offset in the wave (wspan: none)
-    if (t < 8ull * (A.B + 1 - A.b_bkt)) {
-        const u32 b = A.b_bkt + (u32)(t >> 3), j = (u32)(t & 7);
+    u64 rel_lo = wspan, rel_hi = wspan;    // this thread's offsets in the wave (none)
+    u32 step = 0;
+    if (t < pref[nb]) {
+        u32 lo = 0, hi = nb;               // the last i with pref[i] <= t
+        while (hi - lo > 1) {
+            const u32 mid = (lo + hi) >> 1;
+            if (pref[mid] <= t) lo = mid; else hi = mid;
+        }
+        const u32 r = t - pref[lo], j = r & 7, c = r >> 3, b = A.b_bkt + lo;
         const u64 p = A.primes[b];
         u64 k = Lw ? div_rcp(Lw + p - 1, p, A.primes_rcp[b]) : 0;
         if (k < p) k = p;
         const u32 rj = r8(j);
         u64 q = k / 30;
         if (30 * q + rj < k) q++;
-        const u64 n0 = (30 * q + rj) * p;
-        if (n0 - Lw < wspan) rel0 = (u32)(n0 - Lw);
         step = 30 * (u32)p;
+        const u64 n0 = (30 * q + rj) * p + (u64)c * P2_FILL_CHUNK * step;
+        if (n0 - Lw < wspan) {
+            rel_lo = n0 - Lw;
+            rel_hi = pc_min((u64)wspan, rel_lo + (u64)P2_FILL_CHUNK * step);
+        }
     }
     __syncthreads();
     const u32 sp = (u32)A.span;
-    for (u64 rel = rel0; rel < wspan; rel += step) atomicAdd(&hist[(u32)rel / sp], 1u);
+    for (u64 rel = rel_lo; rel < rel_hi; rel += step) atomicAdd(&hist[(u32)rel / sp], 1u);
     __syncthreads();
     for (u32 i = threadIdx.x; i < W; i += blockDim.x) {
         const u32 h = hist[i];
@@ -418,7 +442,7 @@ __global__ void __launch_bounds__(256) p2_bucket_fill_kernel(P2Args A, u64 w0, u
         hist[i] = 0;
     }
     __syncthreads();
-    for (u64 rel = rel0; rel < wspan; rel += step) {
+    for (u64 rel = rel_lo; rel < rel_hi; rel += step) {
         const u32 sl = (u32)rel / sp, r = (u32)rel - sl * sp;
         const u32 pos = (r / 30) * 8 + idx30(r % 30);
         const u32 slot = base[sl] + atomicAdd(&hist[sl], 1u);
@@ -437,8 +461,8 @@ static int run_p2_buckets(pc_ctx* ctx, const P2Args& A, int ctas, size_t smem)
     PC_LAUNCHED(ctx);
     u64 cap = 0;
     PC_TRY(copy_to_host(ctx, &cap, ctx->p2_bkt.p, sizeof(u64)));
-    // bucket entries per wave: 2^26 (256 MiB; pi(1e18)'s P2 at 4 KiB segments 70.7 ms with
-    // 2^24, 57.9 with 2^26, 55.6 with 2^27)
+    // bucket entries per wave: 2^26 (256 MiB; with the fill one thread per (prime, class),
+    // pi(1e18)'s P2 at 4 KiB segments took 70.7 ms with 2^24, 57.9 with 2^26, 55.6 with 2^27)
     constexpr u64 P2_BKT_BUDGET = 1ull << 26;
     if (cap == 0 || cap > P2_BKT_BUDGET) {
         pc_set_error(ctx, "p2 buckets: %llu entries per segment", (unsigned long long)cap);
@@ -449,21 +473,32 @@ static int run_p2_buckets(pc_ctx* ctx, const P2Args& A, int ctas, size_t smem)
     W = pc_min(W, (u64)0xFFFFFFFFu / A.span);   // the fill kernel's offsets inside a wave are 32-bit
     W = pc_min(W, (u64)P2_WAVE_MAX);              // and its per-segment counters fit in shared memory
     if (W == 0) W = 1;
-    const size_t o_n = ((size_t)(W * cap * sizeof(u32)) + 255) / 256 * 256;
-    const size_t o_err = o_n + ((size_t)W * sizeof(u32) + 255) / 256 * 256;
+    const u32 nb = A.B + 1 - A.b_bkt;            // bucket primes
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t o_cnt = 256, o_pref = o_cnt + al((size_t)(nb + 1) * sizeof(u32));
+    const size_t o_bkt = o_pref + al((size_t)(nb + 1) * sizeof(u32));
+    const size_t o_n = o_bkt + al((size_t)(W * cap * sizeof(u32)));
+    const size_t o_err = o_n + al((size_t)W * sizeof(u32));
     PC_TRY(buf_reserve(ctx, ctx->p2_bkt, o_err + 256));
     unsigned char* base = ctx->p2_bkt.as<unsigned char>();
-    u32* d_bkt = (u32*)base;
+    u32* d_cnt = (u32*)(base + o_cnt);
+    u32* d_pref = (u32*)(base + o_pref);
+    u32* d_bkt = (u32*)(base + o_bkt);
     u32* d_n = (u32*)(base + o_n);
     int* d_err = (int*)(base + o_err);
+    // the fill's threads: chunks of every (prime, class), the same layout for every wave
+    p2_bucket_chunks_kernel<<<(nb + 255) / 256, 256, 0, ctx->stream>>>(A, (u32)W, d_cnt);
+    PC_LAUNCHED(ctx);
+    PC_TRY(scan_exclusive_u32_to_u32(ctx, d_cnt, d_pref, nb));
+    u32 threads = 0;
+    PC_TRY(copy_to_host(ctx, &threads, d_pref + nb, sizeof(u32)));
     PC_CUDA(ctx, cudaMemsetAsync(d_err, 0, sizeof(int), ctx->stream));
-    const u64 threads = 8ull * (A.B + 1 - A.b_bkt);
     PC_CUDA(ctx, cudaEventRecord(ctx->ev[4], ctx->stream));
     for (u64 w0 = 0; w0 < A.nseg; w0 += W) {
         const u32 Wc = (u32)pc_min(W, A.nseg - w0);
         PC_CUDA(ctx, cudaMemsetAsync(d_n, 0, Wc * sizeof(u32), ctx->stream));
-        p2_bucket_fill_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(A, w0, Wc, d_bkt, d_n,
-                                                                                          (u32)cap, d_err);
+        p2_bucket_fill_kernel<<<(threads + 255) / 256, 256, 0, ctx->stream>>>(A, w0, Wc, d_pref, nb, d_bkt, d_n,
+                                                                            (u32)cap, d_err);
         PC_LAUNCHED(ctx);
         PC_CUDA(ctx, cudaMemsetAsync(A.queue, 0, 64, ctx->stream));
         P2Args Aw = A;
