@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -345,24 +346,31 @@ def run_reference(args):
 
 
 def run_pi_mode(args):
-    """Whole pi(x) evaluations through the C ABI (all phases), one per step."""
+    """Whole pi(x) evaluations through the C ABI (all phases), one per step; with
+    --mode p2, P2(x, pi(y)) alone, y = alpha * iroot3(x)."""
     import torch
     import paper_1503_01839_gb300 as pc
     from paper_1503_01839_gb300 import build as pcbuild
     pcbuild.build()
-    ctx = pc.Context(0, seg_bytes=args.seg_bytes)
+    ctx = pc.Context(0, seg_bytes=args.seg_bytes, p2_bucket=1 if args.p2_bucket else 0)
+    if args.mode == "p2":
+        y = min(ALPHA * iroot3(X), math.isqrt(X))
+        call = lambda: ctx.p2(X, y)
+    else:
+        call = lambda: ctx.pi_count(X, ALPHA)
     for _ in range(max(1, args.warmup)):
-        ref = ctx.pi_count(X, ALPHA)
+        ref = call()
     ts = []
     for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        assert ctx.pi_count(X, ALPHA) == ref
+        assert call() == ref
         ts.append(time.perf_counter() - t0)
     st = ctx.stats()
-    print(json.dumps({"mode": "pi", "x": X, "alpha": ALPHA, "pi": ref, "ms_per_step": 1000 * statistics.mean(ts),
+    print(json.dumps({"mode": args.mode, "x": X, "alpha": ALPHA, "value": ref,
+                      "p2_bucket": bool(args.p2_bucket), "ms_per_step": 1000 * statistics.mean(ts),
                       "phases_ms": {k: round(st[k], 3) for k in ("ms_tables", "ms_s1", "ms_trivial", "ms_easy",
-                                                                  "ms_hard", "ms_p2")}}), flush=True)
+                                                                  "ms_hard", "ms_p2", "ms_p2_kernel")}}), flush=True)
     ctx.close()
     return 0
 
@@ -495,11 +503,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seg-bytes", type=int, default=0)
+    ap.add_argument("--p2-bucket", action="store_true",
+                    help="pi / p2 modes: P2 by the bucket sieve of Section 2.3 (pc_params.p2_bucket)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-pi", action="store_true", help="skip the pi(1e16)/pi(1e18) wall-time lines")
     ap.add_argument("--x", type=float, default=1e18, help="profiling only: a smaller x than the benchmark's")
     ap.add_argument("--alpha", type=int, default=20)
-    ap.add_argument("--mode", default="s2_hard", choices=["s2_hard", "pi", "batch", "batch-graph", "serve"],
+    ap.add_argument("--mode", default="s2_hard", choices=["s2_hard", "pi", "p2", "batch", "batch-graph", "serve"],
                     help="pi / batch / serve: time only that part; batch-graph: only the batched call, "
                          "twice, no tuning and no plain loop (profiling aids)")
     ap.add_argument("--batch", type=int, default=4096, help="queries of the batched workload (0: skip)")
@@ -513,7 +523,7 @@ def main():
     args = ap.parse_args()
     global X, ALPHA
     X, ALPHA = int(args.x), args.alpha
-    if args.mode == "pi":
+    if args.mode in ("pi", "p2"):
         return run_pi_mode(args)
     if args.mode == "batch":
         print(json.dumps(run_batch(0, args.batch, args.streams)), flush=True)
